@@ -1,0 +1,1003 @@
+/*
+ * hdmc_oracle.c -- plain serial reference implementation of the massively
+ * parallel hard-disk Monte Carlo sweep (Anderson, Jankowski, Grubb, Engel,
+ * Glotzer, "Massively parallel Monte Carlo for many-particle simulations on
+ * GPUs", J. Comput. Phys. 2013).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is
+ * checked against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it.  It shares no code, header, table or
+ * constant generator with the CUDA library; both sides implement Philox4x32-10
+ * independently from its published definition (Salmon, Moraes, Dror, Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ *
+ * Everything here is deliberately plain: one cell at a time, in the order of
+ * the paper's pseudocode, no blocking, no fusion.  Build with
+ *     gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
+ * (-ffp-contract=off matters: the GPU path must agree bit for bit, and gcc on
+ * aarch64 would otherwise fuse a*b+c into one rounding).  An optional
+ * -fopenmp runs the cells of one checkerboard set in parallel; cells of one
+ * set never read each other's data (Sec. 2.1), so the result is identical for
+ * any thread count.
+ *
+ * Two arithmetic modes, fixed at creation:
+ *   prec 0 (FP64): positions are binary64 cell-local offsets.
+ *   prec 1 (FP32): positions are binary32 cell-local offsets (the paper stores
+ *                  single-precision coordinates, Sec. 5); the cell widths used
+ *                  inside the sweep are the binary32 roundings of wx, wy.
+ *
+ * Readings of the paper taken here (each one is listed in the design notes):
+ *  - a cell is the half-open square [0,wx) x [0,wy) in its own frame (Alg. 4
+ *    writes 0 < D <= w, Alg. 2 leaves "in cell" unstated);
+ *  - containment is tested before overlap (same accepted set, Alg. 2);
+ *  - the own-cell overlap candidates are the cell's current (shuffled)
+ *    positions other than the moving one (Alg. 2 reads them from global
+ *    memory, which would be stale);
+ *  - the trial displacement is uniform over a disk of radius d, drawn by
+ *    rejection from a symmetric lattice of points in (-1,1)^2;
+ *  - the grid is mx x my cells, mx (my) the largest even integer <= Lx/sigma
+ *    (Ly/sigma), so that the checkerboard tiles the periodic box (Eq. 1);
+ *  - a migrant re-expressed in the new cell's frame that rounds onto the
+ *    upper cell edge is clamped to the largest representable value below it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_EOVERFLOW 3
+#define ORC_EOVERLAP 4
+#define ORC_ENOMEM 6
+
+#define NMAX 4               /* disks per cell when sigma <= w < sqrt(2) sigma (Sec. 3.1, Fig. 3) */
+#define EMPTY_SLOT (-1.0e4)  /* exported value of an unused slot (Sec. 3.2 uses (-10,-10)) */
+
+/* Philox counter word 2 carries the stream's domain in bits 28..31. */
+#define DOM_SHUFFLE 0u
+#define DOM_TRIAL 1u
+#define DOM_SWEEP 2u
+#define DOM_INIT 3u
+#define DOM_SHIFT 4u
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. SC'11): ten rounds of two 32x32->64 products */
+/* mixed with the counter and a Weyl-sequence key.                           */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod1;
+        uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* A stream of 32-bit words: block b of the stream is Philox(key, (c0,c1,c2,b)),
+ * and its four words are consumed in order. */
+typedef struct {
+    uint32_t key[2];
+    uint32_t c0, c1, c2;
+    uint32_t block;
+    uint32_t buf[4];
+    int pos;
+} stream_t;
+
+static void stream_open(stream_t *s, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = (uint32_t)(seed >> 32);
+    s->c0 = c0; s->c1 = c1; s->c2 = c2;
+    s->block = 0;
+    s->pos = 4;
+}
+
+static uint32_t stream_word(stream_t *s)
+{
+    if (s->pos == 4) {
+        uint32_t ctr[4] = {s->c0, s->c1, s->c2, s->block};
+        orc_philox(ctr, s->key, s->buf);
+        s->block += 1;
+        s->pos = 0;
+    }
+    return s->buf[s->pos++];
+}
+
+/* Uniform integer in [0, range), 1 <= range < 2^32, by Lemire's multiply-high
+ * method with exact rejection (Lemire, "Fast random integer generation in an
+ * interval", ACM TOMACS 2019): the low half of word*range is rejected when it
+ * falls below 2^32 mod range. */
+static int lemire_map(uint32_t word, uint32_t range, uint32_t *value)
+{
+    uint32_t threshold = (uint32_t)(0u - range) % range; /* 2^32 mod range */
+    uint64_t m = (uint64_t)word * (uint64_t)range;
+    *value = (uint32_t)(m >> 32);
+    return (uint32_t)m >= threshold;
+}
+
+static uint32_t stream_bounded(stream_t *s, uint32_t range)
+{
+    uint32_t value;
+    while (!lemire_map(stream_word(s), range, &value)) {
+    }
+    return value;
+}
+
+/* Symmetric binary64 variate: k = top 52 bits of (hi:lo), value (2k+1-2^52) 2^-52.
+ * The 2^52 values are the odd multiples of 2^-52 in (-1,1), mirror-symmetric
+ * about 0, each exactly representable. */
+static double sym52(uint32_t hi, uint32_t lo)
+{
+    uint64_t k = (((uint64_t)hi << 32) | (uint64_t)lo) >> 12;
+    int64_t m = (int64_t)(2 * k + 1) - ((int64_t)1 << 52);
+    return (double)m * 0x1p-52;
+}
+
+/* Symmetric binary32 variate from the top 23 bits of one word. */
+static float sym23(uint32_t w)
+{
+    uint32_t k = w >> 9;
+    int32_t m = (int32_t)(2 * k + 1) - (1 << 23);
+    return (float)m * 0x1p-23f;
+}
+
+/* Uniform binary64 in [0,1) with 53 random bits. */
+static double unif53(uint32_t hi, uint32_t lo)
+{
+    uint64_t k = (((uint64_t)hi << 32) | (uint64_t)lo) >> 11;
+    return (double)k * 0x1p-53;
+}
+
+/* Exposed for the tests. */
+uint32_t orc_stream_bounded(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                            uint32_t range, int64_t count, uint32_t *out)
+{
+    stream_t s;
+    stream_open(&s, seed, c0, c1, c2);
+    for (int64_t i = 0; i < count; ++i)
+        out[i] = stream_bounded(&s, range);
+    return s.block;
+}
+
+void orc_stream_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                      int64_t count, uint32_t *out)
+{
+    stream_t s;
+    stream_open(&s, seed, c0, c1, c2);
+    for (int64_t i = 0; i < count; ++i)
+        out[i] = stream_word(&s);
+}
+
+/* Lemire acceptance count over every 32-bit word for one range <= 16
+ * (exhaustive test of exact uniformity): counts[v] = #words mapping to v. */
+void orc_lemire_exhaustive(uint32_t range, uint64_t *counts)
+{
+    memset(counts, 0, sizeof(uint64_t) * range);
+    /* 2^32 words split into 256 chunks (parallel when built with OpenMP). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int chunk = 0; chunk < 256; ++chunk) {
+        uint64_t local[16] = {0};
+        uint32_t w0 = (uint32_t)chunk << 24;
+        for (uint32_t k = 0; k < (1u << 24); ++k) {
+            uint32_t v;
+            if (lemire_map(w0 + k, range, &v)) local[v & 15] += 1;
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        for (uint32_t v = 0; v < range && v < 16; ++v) counts[v] += local[v];
+    }
+}
+
+double orc_sym52(uint32_t hi, uint32_t lo) { return sym52(hi, lo); }
+float orc_sym23(uint32_t w) { return sym23(w); }
+
+/* ------------------------------------------------------------------------ */
+/* System state                                                              */
+/* ------------------------------------------------------------------------ */
+typedef struct oracle {
+    int64_t N;
+    double Lx, Ly, sigma, d;
+    int nsel;
+    uint64_t seed;
+    int prec;
+    int mx, my;
+    double wx, wy;          /* cell widths, binary64 */
+    float wxf, wyf;         /* binary32 cell widths used by the FP32 mode */
+    int64_t C;              /* mx*my */
+    double *X, *Y;          /* FP64 mode: slot (c,j) at index 4c+j, canonical c = cy*mx+cx */
+    float *Xf, *Yf;         /* FP32 mode */
+    uint8_t *n;             /* disks per cell */
+    double Ox, Oy;          /* accumulated grid origin (Alg. 1, shift_cells) */
+    uint64_t sweep;         /* index of the next sweep */
+    uint64_t shifts;        /* explicit shifts done so far */
+    uint64_t cnt[4];        /* trials, accepted, rejected (left cell), rejected (overlap) */
+    /* balance-control switches (Sec. 2.4): 1 = step performed (default) */
+    int shuffle_particles, shuffle_sets;
+} oracle_t;
+
+static double prev_double(double w) { return nextafter(w, 0.0); }
+static float prev_float(float w) { return nextafterf(w, 0.0f); }
+
+/* Grid rule: mx = largest even integer <= Lx/sigma, likewise my. */
+static int grid_size(double L, double sigma)
+{
+    double q = floor(L / sigma);
+    if (q > 2.0e9) return -1;
+    int m = (int)q;
+    return m - (m & 1);
+}
+
+int orc_grid(double Lx, double Ly, double sigma, int32_t *mx, int32_t *my, double *wx, double *wy)
+{
+    if (!(sigma > 0) || !(Lx > 0) || !(Ly > 0)) return ORC_EINVAL;
+    int a = grid_size(Lx, sigma), b = grid_size(Ly, sigma);
+    if (a < 4 || b < 4) return ORC_EINVAL;
+    *mx = a; *my = b;
+    *wx = Lx / a; *wy = Ly / b;
+    /* n <= 4 needs w < sqrt(2) sigma (Fig. 3): compare w^2 < 2 sigma^2 */
+    if (!((*wx) * (*wx) < 2.0 * sigma * sigma) || !((*wy) * (*wy) < 2.0 * sigma * sigma))
+        return ORC_EINVAL;
+    return ORC_OK;
+}
+
+static int is_set(const oracle_t *o, int64_t c, int j) { return j < o->n[c]; }
+
+static void slot_get(const oracle_t *o, int64_t c, int j, double *x, double *y)
+{
+    if (o->prec == 0) { *x = o->X[4 * c + j]; *y = o->Y[4 * c + j]; }
+    else { *x = (double)o->Xf[4 * c + j]; *y = (double)o->Yf[4 * c + j]; }
+}
+
+void orc_destroy(oracle_t *o)
+{
+    if (!o) return;
+    free(o->X); free(o->Y); free(o->Xf); free(o->Yf); free(o->n);
+    free(o);
+}
+
+static oracle_t *alloc_state(int64_t N, double Lx, double Ly, double sigma, double d,
+                             int nsel, uint64_t seed, int prec, int *err)
+{
+    int32_t mx, my;
+    double wx, wy;
+    *err = ORC_EINVAL;
+    if (N < 1 || nsel < 1 || nsel > 255 || (prec != 0 && prec != 1)) return NULL;
+    if (orc_grid(Lx, Ly, sigma, &mx, &my, &wx, &wy) != ORC_OK) return NULL;
+    if (!(d > 0) || !(d < 0.5 * wx) || !(d < 0.5 * wy)) return NULL;
+    if ((int64_t)mx * my * NMAX < N) return NULL;
+    oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
+    *err = ORC_ENOMEM;
+    if (!o) return NULL;
+    o->N = N; o->Lx = Lx; o->Ly = Ly; o->sigma = sigma; o->d = d;
+    o->nsel = nsel; o->seed = seed; o->prec = prec;
+    o->mx = mx; o->my = my; o->wx = wx; o->wy = wy;
+    o->wxf = (float)wx; o->wyf = (float)wy;
+    o->C = (int64_t)mx * my;
+    o->shuffle_particles = 1; o->shuffle_sets = 1;
+    o->n = (uint8_t *)calloc((size_t)o->C, 1);
+    if (prec == 0) {
+        o->X = (double *)malloc(sizeof(double) * 4 * (size_t)o->C);
+        o->Y = (double *)malloc(sizeof(double) * 4 * (size_t)o->C);
+        if (!o->X || !o->Y || !o->n) { orc_destroy(o); return NULL; }
+    } else {
+        o->Xf = (float *)malloc(sizeof(float) * 4 * (size_t)o->C);
+        o->Yf = (float *)malloc(sizeof(float) * 4 * (size_t)o->C);
+        if (!o->Xf || !o->Yf || !o->n) { orc_destroy(o); return NULL; }
+    }
+    *err = ORC_OK;
+    return o;
+}
+
+/* Bin one global position (x in [0,Lx], y in [0,Ly]) into a cell and a local
+ * offset: cx = trunc(x/wx) clamped, then corrected by one cell if the
+ * rounded local offset falls outside [0,wx); finally clamped into [0,wx). */
+static void bin_axis(double x, double w, int m, int *cell, double *loc)
+{
+    int c = (int)(x / w);
+    if (c > m - 1) c = m - 1;
+    if (c < 0) c = 0;
+    double l = x - (double)c * w;
+    if (l < 0.0 && c > 0) { c -= 1; l = x - (double)c * w; }
+    if (l >= w && c < m - 1) { c += 1; l = x - (double)c * w; }
+    if (l < 0.0) l = 0.0;
+    if (l >= w) l = prev_double(w);
+    *cell = c;
+    *loc = l;
+}
+
+/* Overlap test of every disk against the disks of its 3x3 neighbourhood, in
+ * cell-local frames (same arithmetic as the sweep).  Returns #overlapping
+ * ordered pairs. */
+static int64_t count_overlaps_local(const oracle_t *o)
+{
+    int64_t bad = 0;
+    for (int cy = 0; cy < o->my; ++cy)
+        for (int cx = 0; cx < o->mx; ++cx) {
+            int64_t c = (int64_t)cy * o->mx + cx;
+            for (int i = 0; i < o->n[c]; ++i) {
+                double px, py;
+                slot_get(o, c, i, &px, &py);
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int ncx = (cx + dx + o->mx) % o->mx, ncy = (cy + dy + o->my) % o->my;
+                        int64_t nc = (int64_t)ncy * o->mx + ncx;
+                        for (int j = 0; j < o->n[nc]; ++j) {
+                            if (nc == c && j == i && dx == 0 && dy == 0) continue;
+                            double qx, qy;
+                            slot_get(o, nc, j, &qx, &qy);
+                            if (o->prec == 0) {
+                                double ex = qx + (double)dx * o->wx, ey = qy + (double)dy * o->wy;
+                                double ddx = px - ex, ddy = py - ey;
+                                if (ddx * ddx + ddy * ddy < o->sigma * o->sigma) bad++;
+                            } else {
+                                float ex = (float)qx + (float)dx * o->wxf;
+                                float ey = (float)qy + (float)dy * o->wyf;
+                                float ddx = (float)px - ex, ddy = (float)py - ey;
+                                if (fmaf(ddx, ddx, ddy * ddy) < (float)(o->sigma * o->sigma)) bad++;
+                            }
+                        }
+                    }
+            }
+        }
+    return bad;
+}
+
+/* Place global positions xy[2N] into the cell structure (slot order within a
+ * cell = ascending particle index). */
+static int place(oracle_t *o, const double *xy)
+{
+    memset(o->n, 0, (size_t)o->C);
+    for (int64_t c = 0; c < 4 * o->C; ++c) {
+        if (o->prec == 0) { o->X[c] = EMPTY_SLOT; o->Y[c] = EMPTY_SLOT; }
+        else { o->Xf[c] = (float)EMPTY_SLOT; o->Yf[c] = (float)EMPTY_SLOT; }
+    }
+    for (int64_t p = 0; p < o->N; ++p) {
+        double x = xy[2 * p], y = xy[2 * p + 1];
+        if (!(x >= 0.0 && x <= o->Lx && y >= 0.0 && y <= o->Ly)) return ORC_EINVAL;
+        int cx, cy;
+        double lx, ly;
+        bin_axis(x, o->wx, o->mx, &cx, &lx);
+        bin_axis(y, o->wy, o->my, &cy, &ly);
+        int64_t c = (int64_t)cy * o->mx + cx;
+        if (o->n[c] >= NMAX) return ORC_EOVERFLOW;
+        int j = o->n[c]++;
+        if (o->prec == 0) { o->X[4 * c + j] = lx; o->Y[4 * c + j] = ly; }
+        else {
+            float fx = (float)lx, fy = (float)ly;
+            if (fx >= o->wxf) fx = prev_float(o->wxf);
+            if (fy >= o->wyf) fy = prev_float(o->wyf);
+            o->Xf[4 * c + j] = fx; o->Yf[4 * c + j] = fy;
+        }
+    }
+    if (count_overlaps_local(o) != 0) return ORC_EOVERLAP;
+    return ORC_OK;
+}
+
+/* Hexagonal start: choose nx*ny = N, ny even, making the row spacing Ly/ny
+ * closest (in ratio) to sqrt(3)/2 times the column spacing Lx/nx. */
+int orc_lattice_shape(int64_t N, double Lx, double Ly, int64_t *nx_out, int64_t *ny_out)
+{
+    int64_t best_nx = -1, best_ny = -1;
+    double best = 0.0;
+    for (int64_t ny = 2; ny <= N; ny += 2) {
+        if (N % ny) continue;
+        int64_t nx = N / ny;
+        double cost = fabs(log((Ly / (double)ny) / ((Lx / (double)nx) * 0.86602540378443864676)));
+        if (best_nx < 0 || cost < best) { best = cost; best_nx = nx; best_ny = ny; }
+    }
+    if (best_nx < 0) return ORC_EINVAL;
+    *nx_out = best_nx; *ny_out = best_ny;
+    return ORC_OK;
+}
+
+/* Lattice site p = j*nx + i at ((i + 1/2 + (j mod 2)/2) Lx/nx, (j + 1/2) Ly/ny),
+ * displaced uniformly within a disk of radius 0.01 sigma (init stream of p),
+ * wrapped into the box. */
+int orc_lattice_positions(int64_t N, double Lx, double Ly, double sigma, uint64_t seed, double *xy)
+{
+    int64_t nx, ny;
+    if (orc_lattice_shape(N, Lx, Ly, &nx, &ny) != ORC_OK) return ORC_EINVAL;
+    double ax = Lx / (double)nx, ay = Ly / (double)ny, rj = 0.01 * sigma;
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t p = j * nx + i;
+            double x0 = ((double)i + 0.5 + 0.5 * (double)(j & 1)) * ax;
+            double y0 = ((double)j + 0.5) * ay;
+            stream_t s;
+            stream_open(&s, seed, (uint32_t)p, 0xFFFFFFFEu, DOM_INIT << 28);
+            double u, v;
+            do {
+                uint32_t a = stream_word(&s), b = stream_word(&s), c = stream_word(&s), e = stream_word(&s);
+                u = sym52(a, b);
+                v = sym52(c, e);
+            } while (!(u * u + v * v < 1.0));
+            double x = x0 + rj * u, y = y0 + rj * v;
+            if (x >= Lx) x -= Lx;
+            if (x < 0.0) x += Lx;
+            if (y >= Ly) y -= Ly;
+            if (y < 0.0) y += Ly;
+            xy[2 * p] = x;
+            xy[2 * p + 1] = y;
+        }
+    return ORC_OK;
+}
+
+int orc_create(oracle_t **out, int64_t N, double Lx, double Ly, double sigma, double d,
+               int nsel, uint64_t seed, int prec)
+{
+    int err;
+    *out = NULL;
+    if (N < 2 || (N & 1)) return ORC_EINVAL;
+    oracle_t *o = alloc_state(N, Lx, Ly, sigma, d, nsel, seed, prec, &err);
+    if (!o) return err;
+    double *xy = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    if (!xy) { orc_destroy(o); return ORC_ENOMEM; }
+    err = orc_lattice_positions(N, Lx, Ly, sigma, seed, xy);
+    if (err == ORC_OK) err = place(o, xy);
+    free(xy);
+    if (err != ORC_OK) { orc_destroy(o); return err; }
+    *out = o;
+    return ORC_OK;
+}
+
+int orc_create_from(oracle_t **out, int64_t N, double Lx, double Ly, double sigma, double d,
+                    int nsel, uint64_t seed, int prec, const double *xy)
+{
+    int err;
+    *out = NULL;
+    oracle_t *o = alloc_state(N, Lx, Ly, sigma, d, nsel, seed, prec, &err);
+    if (!o) return err;
+    err = place(o, xy);
+    if (err != ORC_OK) { orc_destroy(o); return err; }
+    *out = o;
+    return ORC_OK;
+}
+
+int orc_set_move_size(oracle_t *o, double d)
+{
+    if (!(d > 0) || !(d < 0.5 * o->wx) || !(d < 0.5 * o->wy)) return ORC_EINVAL;
+    o->d = d;
+    return ORC_OK;
+}
+
+void orc_set_balance(oracle_t *o, int shuffle_particles, int shuffle_sets)
+{
+    o->shuffle_particles = shuffle_particles;
+    o->shuffle_sets = shuffle_sets;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sweep-level draws (Alg. 1): set order by Fisher-Yates, shift direction f  */
+/* in {+x,-x,+y,-y}, shift distance d ~ U(0, w/2) along f's axis.            */
+/* ------------------------------------------------------------------------ */
+typedef struct { int perm[4]; int fdir; double ds; } draws_t;
+
+static void sweep_draws(uint64_t seed, uint32_t sweep, double wx, double wy, draws_t *r)
+{
+    stream_t s;
+    stream_open(&s, seed, sweep, 0xFFFFFFFFu, DOM_SWEEP << 28);
+    for (int q = 0; q < 4; ++q) r->perm[q] = q;
+    for (int j = 3; j >= 1; --j) {
+        int k = (int)stream_bounded(&s, (uint32_t)(j + 1));
+        int t = r->perm[j]; r->perm[j] = r->perm[k]; r->perm[k] = t;
+    }
+    r->fdir = (int)stream_bounded(&s, 4u);
+    uint32_t hi = stream_word(&s), lo = stream_word(&s);
+    double w = (r->fdir >> 1) ? wy : wx;
+    r->ds = unif53(hi, lo) * (0.5 * w);
+}
+
+static void shift_draws(uint64_t seed, uint32_t index, double wx, double wy, draws_t *r)
+{
+    stream_t s;
+    stream_open(&s, seed, index, 0xFFFFFFFFu, DOM_SHIFT << 28);
+    for (int q = 0; q < 4; ++q) r->perm[q] = q;
+    r->fdir = (int)stream_bounded(&s, 4u);
+    uint32_t hi = stream_word(&s), lo = stream_word(&s);
+    double w = (r->fdir >> 1) ? wy : wx;
+    r->ds = unif53(hi, lo) * (0.5 * w);
+}
+
+void orc_sweep_draws(uint64_t seed, uint32_t sweep, double wx, double wy, int32_t perm[4],
+                     int32_t *fdir, double *ds)
+{
+    draws_t r;
+    sweep_draws(seed, sweep, wx, wy, &r);
+    for (int q = 0; q < 4; ++q) perm[q] = r.perm[q];
+    *fdir = r.fdir;
+    *ds = r.ds;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Per-cell random draws of a sub-sweep (Alg. 1 lines 5 and 8).              */
+/* ------------------------------------------------------------------------ */
+
+/* Fisher-Yates shuffle of slots 0..n-1 (Durstenfeld): for j = n-1 down to 1
+ * swap positions j and k_j, k_j uniform in [0, j].  On return perm[j] is the
+ * old slot that now sits in slot j. */
+static void shuffle_order(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int perm[4])
+{
+    stream_t s;
+    stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | ((uint32_t)Q << 24));
+    for (int j = 0; j < 4; ++j) perm[j] = j;
+    for (int j = n - 1; j >= 1; --j) {
+        int k = (int)stream_bounded(&s, (uint32_t)(j + 1));
+        int t = perm[j]; perm[j] = perm[k]; perm[k] = t;
+    }
+}
+
+/* Trial displacement direction (u,v), uniform over the unit disk by
+ * rejection: binary64 mode takes 4 words per attempt. */
+static void displacement64(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int t, double *u, double *v)
+{
+    stream_t s;
+    stream_open(&s, seed, sweep, cell, (DOM_TRIAL << 28) | ((uint32_t)Q << 24) | (uint32_t)t);
+    do {
+        uint32_t a = stream_word(&s), b = stream_word(&s), e = stream_word(&s), f = stream_word(&s);
+        *u = sym52(a, b);
+        *v = sym52(e, f);
+    } while (!(*u * *u + *v * *v < 1.0));
+}
+
+/* binary32 mode: 2 words per attempt; u^2 + v^2 evaluated as fmaf(u,u,v*v). */
+static void displacement32(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int t, float *u, float *v)
+{
+    stream_t s;
+    stream_open(&s, seed, sweep, cell, (DOM_TRIAL << 28) | ((uint32_t)Q << 24) | (uint32_t)t);
+    do {
+        uint32_t a = stream_word(&s), b = stream_word(&s);
+        *u = sym23(a);
+        *v = sym23(b);
+    } while (!(fmaf(*u, *u, *v * *v) < 1.0f));
+}
+
+/* Test hooks. */
+void orc_displacements(uint64_t seed, uint32_t sweep, int Q, int t, int prec, int64_t ncells, double *uv)
+{
+    for (int64_t c = 0; c < ncells; ++c) {
+        if (prec == 0) {
+            displacement64(seed, sweep, (uint32_t)c, Q, t, &uv[2 * c], &uv[2 * c + 1]);
+        } else {
+            float u, v;
+            displacement32(seed, sweep, (uint32_t)c, Q, t, &u, &v);
+            uv[2 * c] = u; uv[2 * c + 1] = v;
+        }
+    }
+}
+
+void orc_shuffles(uint64_t seed, uint32_t sweep, int Q, int n, int64_t ncells, int32_t *perms)
+{
+    for (int64_t c = 0; c < ncells; ++c) {
+        int p[4];
+        shuffle_order(seed, sweep, (uint32_t)c, Q, n, p);
+        for (int j = 0; j < 4; ++j) perms[4 * c + j] = p[j];
+    }
+}
+
+/* Slot visited by trial t of a cell holding n disks: t mod n (Alg. 1 line 7). */
+static int visit_slot(int t, int n) { return t % n; }
+
+void orc_visit_sequence(int n, int nsel, int32_t *seq)
+{
+    for (int t = 0; t < nsel; ++t) seq[t] = visit_slot(t, n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One cell update of a sub-sweep (Alg. 1 lines 5-11, Alg. 2)                */
+/* ------------------------------------------------------------------------ */
+static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, uint64_t acc[4])
+{
+    int64_t c = (int64_t)cy * o->mx + cx;
+    int n = o->n[c];
+    if (n == 0) return;
+    double *X = o->X + 4 * c, *Y = o->Y + 4 * c;
+    /* shuffle the cell's particles (Fisher-Yates) */
+    if (o->shuffle_particles && n >= 2) {
+        int perm[4];
+        shuffle_order(o->seed, sweep, (uint32_t)c, Q, n, perm);
+        double tx[4], ty[4];
+        for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
+        for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
+    }
+    const double sig2 = o->sigma * o->sigma;
+    for (int t = 0; t < o->nsel; ++t) {
+        int i = visit_slot(t, n);
+        double u, v;
+        displacement64(o->seed, sweep, (uint32_t)c, Q, t, &u, &v);
+        double nx = X[i] + o->d * u;
+        double ny = Y[i] + o->d * v;
+        acc[0]++;
+        if (!(nx >= 0.0 && nx < o->wx && ny >= 0.0 && ny < o->wy)) { acc[2]++; continue; }
+        int overlap = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double ddx = nx - X[j], ddy = ny - Y[j];
+            if (ddx * ddx + ddy * ddy < sig2) overlap = 1;
+        }
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                int ncx = (cx + dx + o->mx) % o->mx, ncy = (cy + dy + o->my) % o->my;
+                int64_t nc = (int64_t)ncy * o->mx + ncx;
+                double sx = (double)dx * o->wx, sy = (double)dy * o->wy;
+                for (int j = 0; j < o->n[nc]; ++j) {
+                    double ex = o->X[4 * nc + j] + sx, ey = o->Y[4 * nc + j] + sy;
+                    double ddx = nx - ex, ddy = ny - ey;
+                    if (ddx * ddx + ddy * ddy < sig2) overlap = 1;
+                }
+            }
+        if (overlap) { acc[3]++; continue; }
+        X[i] = nx;
+        Y[i] = ny;
+        acc[1]++;
+    }
+}
+
+static void cell_update32(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, uint64_t acc[4])
+{
+    int64_t c = (int64_t)cy * o->mx + cx;
+    int n = o->n[c];
+    if (n == 0) return;
+    float *X = o->Xf + 4 * c, *Y = o->Yf + 4 * c;
+    if (o->shuffle_particles && n >= 2) {
+        int perm[4];
+        shuffle_order(o->seed, sweep, (uint32_t)c, Q, n, perm);
+        float tx[4], ty[4];
+        for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
+        for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
+    }
+    const float sig2 = (float)(o->sigma * o->sigma);
+    const float df = (float)o->d;
+    for (int t = 0; t < o->nsel; ++t) {
+        int i = visit_slot(t, n);
+        float u, v;
+        displacement32(o->seed, sweep, (uint32_t)c, Q, t, &u, &v);
+        float nx = fmaf(df, u, X[i]);
+        float ny = fmaf(df, v, Y[i]);
+        acc[0]++;
+        if (!(nx >= 0.0f && nx < o->wxf && ny >= 0.0f && ny < o->wyf)) { acc[2]++; continue; }
+        int overlap = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            float ddx = nx - X[j], ddy = ny - Y[j];
+            if (fmaf(ddx, ddx, ddy * ddy) < sig2) overlap = 1;
+        }
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                int ncx = (cx + dx + o->mx) % o->mx, ncy = (cy + dy + o->my) % o->my;
+                int64_t nc = (int64_t)ncy * o->mx + ncx;
+                float sx = (float)dx * o->wxf, sy = (float)dy * o->wyf;
+                for (int j = 0; j < o->n[nc]; ++j) {
+                    float ex = o->Xf[4 * nc + j] + sx, ey = o->Yf[4 * nc + j] + sy;
+                    float ddx = nx - ex, ddy = ny - ey;
+                    if (fmaf(ddx, ddx, ddy * ddy) < sig2) overlap = 1;
+                }
+            }
+        if (overlap) { acc[3]++; continue; }
+        X[i] = nx;
+        Y[i] = ny;
+        acc[1]++;
+    }
+}
+
+/* All cells of checkerboard set Q (Eq. 1: Q = (cx mod 2) + 2 (cy mod 2)),
+ * i.e. lines 4-13 of Alg. 1.  Cells of one set are independent. */
+static void subsweep(oracle_t *o, uint32_t sweep, int Q)
+{
+    int qx = Q & 1, qy = Q >> 1;
+    uint64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3)
+#endif
+    for (int cy = qy; cy < o->my; cy += 2) {
+        uint64_t acc[4] = {0, 0, 0, 0};
+        for (int cx = qx; cx < o->mx; cx += 2) {
+            if (o->prec == 0) cell_update64(o, sweep, Q, cx, cy, acc);
+            else cell_update32(o, sweep, Q, cx, cy, acc);
+        }
+        t0 += acc[0]; t1 += acc[1]; t2 += acc[2]; t3 += acc[3];
+    }
+    o->cnt[0] += t0; o->cnt[1] += t1; o->cnt[2] += t2; o->cnt[3] += t3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell shift (Alg. 4): translate every disk by -f*ds.  New cell c keeps the */
+/* disks of old c that stay inside it (old slot order), then takes the disks */
+/* of old c+f that leave c+f, re-expressed in c's frame.  The ownership test */
+/* is the same expression in both places, so no disk is lost (Sec. 3.2).    */
+/* ------------------------------------------------------------------------ */
+static int shift_cells(oracle_t *o, int fdir, double ds)
+{
+    int ax = fdir >> 1;
+    int sgn = (fdir & 1) ? -1 : 1;
+    int64_t C = o->C;
+    uint8_t *nn = (uint8_t *)calloc((size_t)C, 1);
+    int overflow = 0;
+    if (o->prec == 0) {
+        double w = ax ? o->wy : o->wx;
+        double sd = (double)sgn * ds;
+        double sw = (double)sgn * w;
+        double *NX = (double *)malloc(sizeof(double) * 4 * (size_t)C);
+        double *NY = (double *)malloc(sizeof(double) * 4 * (size_t)C);
+        for (int cy = 0; cy < o->my; ++cy)
+            for (int cx = 0; cx < o->mx; ++cx) {
+                int64_t c = (int64_t)cy * o->mx + cx;
+                int ncx = ax ? cx : (cx + sgn + o->mx) % o->mx;
+                int ncy = ax ? (cy + sgn + o->my) % o->my : cy;
+                int64_t nb = (int64_t)ncy * o->mx + ncx;
+                double ox[8], oy[8];
+                int k = 0;
+                for (int j = 0; j < o->n[c]; ++j) {
+                    double px = o->X[4 * c + j], py = o->Y[4 * c + j];
+                    double dp = (ax ? py : px) - sd;
+                    if (dp >= 0.0 && dp < w) {
+                        ox[k] = ax ? px : dp; oy[k] = ax ? dp : py; k++;
+                    }
+                }
+                for (int j = 0; j < o->n[nb]; ++j) {
+                    double px = o->X[4 * nb + j], py = o->Y[4 * nb + j];
+                    double dp = (ax ? py : px) - sd;
+                    if (!(dp >= 0.0 && dp < w)) {
+                        double v = dp + sw;
+                        if (v >= w) v = prev_double(w);
+                        if (v < 0.0) v = 0.0;
+                        ox[k] = ax ? px : v; oy[k] = ax ? v : py; k++;
+                    }
+                }
+                if (k > NMAX) { overflow = 1; k = NMAX; }
+                nn[c] = (uint8_t)k;
+                for (int j = 0; j < 4; ++j) {
+                    NX[4 * c + j] = j < k ? ox[j] : EMPTY_SLOT;
+                    NY[4 * c + j] = j < k ? oy[j] : EMPTY_SLOT;
+                }
+            }
+        free(o->X); free(o->Y);
+        o->X = NX; o->Y = NY;
+        if (ax) o->Oy += sd; else o->Ox += sd;
+    } else {
+        float w = ax ? o->wyf : o->wxf;
+        float dsf = (float)ds;
+        float sd = (float)sgn * dsf;
+        float sw = (float)sgn * w;
+        float *NX = (float *)malloc(sizeof(float) * 4 * (size_t)C);
+        float *NY = (float *)malloc(sizeof(float) * 4 * (size_t)C);
+        for (int cy = 0; cy < o->my; ++cy)
+            for (int cx = 0; cx < o->mx; ++cx) {
+                int64_t c = (int64_t)cy * o->mx + cx;
+                int ncx = ax ? cx : (cx + sgn + o->mx) % o->mx;
+                int ncy = ax ? (cy + sgn + o->my) % o->my : cy;
+                int64_t nb = (int64_t)ncy * o->mx + ncx;
+                float ox[8], oy[8];
+                int k = 0;
+                for (int j = 0; j < o->n[c]; ++j) {
+                    float px = o->Xf[4 * c + j], py = o->Yf[4 * c + j];
+                    float dp = (ax ? py : px) - sd;
+                    if (dp >= 0.0f && dp < w) {
+                        ox[k] = ax ? px : dp; oy[k] = ax ? dp : py; k++;
+                    }
+                }
+                for (int j = 0; j < o->n[nb]; ++j) {
+                    float px = o->Xf[4 * nb + j], py = o->Yf[4 * nb + j];
+                    float dp = (ax ? py : px) - sd;
+                    if (!(dp >= 0.0f && dp < w)) {
+                        float v = dp + sw;
+                        if (v >= w) v = prev_float(w);
+                        if (v < 0.0f) v = 0.0f;
+                        ox[k] = ax ? px : v; oy[k] = ax ? v : py; k++;
+                    }
+                }
+                if (k > NMAX) { overflow = 1; k = NMAX; }
+                nn[c] = (uint8_t)k;
+                for (int j = 0; j < 4; ++j) {
+                    NX[4 * c + j] = j < k ? ox[j] : (float)EMPTY_SLOT;
+                    NY[4 * c + j] = j < k ? oy[j] : (float)EMPTY_SLOT;
+                }
+            }
+        free(o->Xf); free(o->Yf);
+        o->Xf = NX; o->Yf = NY;
+        if (ax) o->Oy += (double)sd; else o->Ox += (double)sd;
+    }
+    free(o->n);
+    o->n = nn;
+    return overflow ? ORC_EOVERFLOW : ORC_OK;
+}
+
+/* n full sweeps (Alg. 1). */
+int orc_sweep(oracle_t *o, int64_t nsweeps)
+{
+    for (int64_t k = 0; k < nsweeps; ++k) {
+        uint32_t sweep = (uint32_t)o->sweep;
+        draws_t r;
+        sweep_draws(o->seed, sweep, o->wx, o->wy, &r);
+        for (int q = 0; q < 4; ++q) {
+            int Q = o->shuffle_sets ? r.perm[q] : q;
+            subsweep(o, sweep, Q);
+        }
+        int err = shift_cells(o, r.fdir, r.ds);
+        o->sweep += 1;
+        if (err != ORC_OK) return err;
+    }
+    return ORC_OK;
+}
+
+/* One explicit extra shift drawn from its own stream (index = #shifts so far). */
+int orc_shift(oracle_t *o)
+{
+    draws_t r;
+    shift_draws(o->seed, (uint32_t)o->shifts, o->wx, o->wy, &r);
+    o->shifts += 1;
+    return shift_cells(o, r.fdir, r.ds);
+}
+
+/* One sub-sweep of set Q with the draws of sweep index `sweep` (tests only). */
+void orc_subsweep(oracle_t *o, uint32_t sweep, int Q) { subsweep(o, sweep, Q); }
+
+/* ------------------------------------------------------------------------ */
+/* Accessors                                                                 */
+/* ------------------------------------------------------------------------ */
+void orc_info(const oracle_t *o, int32_t *mx, int32_t *my, double *wx, double *wy,
+              uint64_t *sweep, uint64_t *shifts)
+{
+    *mx = o->mx; *my = o->my; *wx = o->wx; *wy = o->wy;
+    *sweep = o->sweep; *shifts = o->shifts;
+}
+
+void orc_counters(const oracle_t *o, uint64_t out[4])
+{
+    for (int k = 0; k < 4; ++k) out[k] = o->cnt[k];
+}
+
+void orc_origin(const oracle_t *o, double out[2]) { out[0] = o->Ox; out[1] = o->Oy; }
+
+/* Raw state in canonical order: local[(4c+j)*2 + {0,1}], counts[c]; unused
+ * slots read EMPTY_SLOT. */
+void orc_state(const oracle_t *o, double *local, uint8_t *counts)
+{
+    for (int64_t c = 0; c < o->C; ++c) {
+        counts[c] = o->n[c];
+        for (int j = 0; j < 4; ++j) {
+            double x = EMPTY_SLOT, y = EMPTY_SLOT;
+            if (is_set(o, c, j)) slot_get(o, c, j, &x, &y);
+            local[2 * (4 * c + j)] = x;
+            local[2 * (4 * c + j) + 1] = y;
+        }
+    }
+}
+
+/* Global coordinates in canonical (cell, slot) order:
+ *   g = O + (cell*w + local), wrapped into [0, m*w) by g - L floor(g/L),
+ * with w the mode's cell width (binary32 widths in FP32 mode). */
+void orc_positions(const oracle_t *o, double *xy)
+{
+    double wx = o->prec == 0 ? o->wx : (double)o->wxf;
+    double wy = o->prec == 0 ? o->wy : (double)o->wyf;
+    double Lx = o->prec == 0 ? o->Lx : (double)o->mx * wx;
+    double Ly = o->prec == 0 ? o->Ly : (double)o->my * wy;
+    int64_t p = 0;
+    for (int cy = 0; cy < o->my; ++cy)
+        for (int cx = 0; cx < o->mx; ++cx) {
+            int64_t c = (int64_t)cy * o->mx + cx;
+            for (int j = 0; j < o->n[c]; ++j) {
+                double lx, ly;
+                slot_get(o, c, j, &lx, &ly);
+                double gx = o->Ox + ((double)cx * wx + lx);
+                double gy = o->Oy + ((double)cy * wy + ly);
+                gx = gx - Lx * floor(gx / Lx);
+                gy = gy - Ly * floor(gy / Ly);
+                xy[2 * p] = gx;
+                xy[2 * p + 1] = gy;
+                p++;
+            }
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Contact histogram (Sec. 4): ordered pairs (i, j != i) at distance r with  */
+/* sigma <= r < sigma + nbins*dr, bin floor((r - sigma)/dr).  Distances are  */
+/* taken in cell-local frames over the 5x5 cell neighbourhood (w >= sigma,   */
+/* so two rings reach past sigma + c for c <= sigma), in binary64.          */
+/* ------------------------------------------------------------------------ */
+void orc_histogram(const oracle_t *o, int nbins, double dr, uint64_t *hist)
+{
+    memset(hist, 0, sizeof(uint64_t) * (size_t)nbins);
+    double wx = o->prec == 0 ? o->wx : (double)o->wxf;
+    double wy = o->prec == 0 ? o->wy : (double)o->wyf;
+    double sigma = o->sigma;
+    for (int cy = 0; cy < o->my; ++cy)
+        for (int cx = 0; cx < o->mx; ++cx) {
+            int64_t c = (int64_t)cy * o->mx + cx;
+            for (int i = 0; i < o->n[c]; ++i) {
+                double px, py;
+                slot_get(o, c, i, &px, &py);
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        int ncx = ((cx + dx) % o->mx + o->mx) % o->mx;
+                        int ncy = ((cy + dy) % o->my + o->my) % o->my;
+                        int64_t nc = (int64_t)ncy * o->mx + ncx;
+                        double sx = (double)dx * wx, sy = (double)dy * wy;
+                        for (int j = 0; j < o->n[nc]; ++j) {
+                            if (dx == 0 && dy == 0 && j == i) continue;
+                            double qx, qy;
+                            slot_get(o, nc, j, &qx, &qy);
+                            double ddx = px - (qx + sx), ddy = py - (qy + sy);
+                            double r = sqrt(ddx * ddx + ddy * ddy);
+                            double t = (r - sigma) / dr;
+                            if (t >= 0.0 && t < (double)nbins) hist[(int)t] += 1;
+                        }
+                    }
+            }
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute-force checks on global coordinates (tests)                          */
+/* ------------------------------------------------------------------------ */
+static double min_image(double d, double L)
+{
+    return d - L * floor(d / L + 0.5);
+}
+
+/* #unordered pairs with minimum-image distance < rmin. */
+int64_t orc_bruteforce_close_pairs(const double *xy, int64_t N, double Lx, double Ly, double rmin)
+{
+    int64_t bad = 0;
+    double r2min = rmin * rmin;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i + 1; j < N; ++j) {
+            double dx = min_image(xy[2 * i] - xy[2 * j], Lx);
+            double dy = min_image(xy[2 * i + 1] - xy[2 * j + 1], Ly);
+            if (dx * dx + dy * dy < r2min) bad++;
+        }
+    return bad;
+}
+
+/* Ordered-pair distance histogram by brute force over all pairs and the 3x3
+ * periodic images (global coordinates), same binning rule as above. */
+void orc_bruteforce_histogram(const double *xy, int64_t N, double Lx, double Ly, double sigma,
+                              int nbins, double dr, uint64_t *hist)
+{
+    memset(hist, 0, sizeof(uint64_t) * (size_t)nbins);
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            for (int iy = -1; iy <= 1; ++iy)
+                for (int ix = -1; ix <= 1; ++ix) {
+                    if (i == j && ix == 0 && iy == 0) continue;
+                    double dx = xy[2 * i] - (xy[2 * j] + (double)ix * Lx);
+                    double dy = xy[2 * i + 1] - (xy[2 * j + 1] + (double)iy * Ly);
+                    double r = sqrt(dx * dx + dy * dy);
+                    double t = (r - sigma) / dr;
+                    if (t >= 0.0 && t < (double)nbins) hist[(int)t] += 1;
+                }
+        }
+}
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int orc_local_overlaps(const oracle_t *o) { return (int)count_overlaps_local(o); }
