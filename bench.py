@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the checkerboard hard-disk Monte Carlo sweep on GB300.
+
+Workload (synthetic, generated here): N = 1024^2 hard disks of diameter 1 in
+the periodic box of a 1024 x 1024 hexagonal patch at packing fraction
+phi = 0.716 (1152.45 x 998.06), hexagonal start with 0.01 sigma jitter,
+maximum displacement d = 0.08 sigma, n_M = 4 trial moves per cell and
+sub-sweep.  One step = 100 sweeps (Alg. 1: 4 sub-sweeps + 1 cell shift each)
++ one contact histogram + the pressure fit (Sec. 4), i.e. every stage of the
+hot path.  Metric: attempted trial moves per second (Sec. 5.1), counted by
+the library's trial counters, for the binary32 cell-local path; the binary64
+path is timed on the same workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hdmc|reference]
+
+With torchrun (N > 1) every rank runs an independent replica (seed 1+rank);
+the value is the sum of trial moves over ranks divided by the slowest
+rank's time ("replicas only": the method has no cross-replica exchange).
+--impl reference times the CPU oracle (all host cores) on the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 100
+METRIC = "trial moves/sec at N=1M phi=0.716 (1 GB300), FP32-local vs FP64; % HBM roofline"
+KERNELS_PER_SWEEP = 5          # 4 sub-sweeps + 1 cell shift
+GRAPH_CHUNK = 64               # sweeps per recorded graph (one draws kernel each)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hdmc", choices=["hdmc", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the binary64 path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1211_1646_gb300 import workloads
+    return workloads.n1m_phi0716("fp32")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=10)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_identifier(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return dev
+
+
+def run_hdmc(args, rank, world, dist):
+    import numpy as np
+    import torch
+    from paper_1211_1646_gb300 import build, hdmc
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    seed = 1 + rank
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def one_step(sysm):
+        sysm.sweep(SWEEPS_PER_STEP)
+        sysm.sample()
+        return sysm.pressure()
+
+    def timed_steps(sysm, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            one_step(sysm)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        c0 = int(sysm.counters()[0])
+        total_ms = 0.0
+        pressures = []
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for _ in range(steps):
+                flush.fill_(1)                      # L2 flushed between timed steps (untimed)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bp, g0, _, _ = one_step(sysm)
+                e1.record(stream)
+                e1.synchronize()
+                total_ms += e0.elapsed_time(e1)
+                pressures.append(bp)
+        torch.cuda.synchronize(dev)
+        barrier()
+        trials = int(sysm.counters()[0]) - c0
+        return trials, total_ms, pressures
+
+    # ---- binary32 cell-local path (the headline) ----
+    s32 = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, seed, "fp32", device=dev)
+    sampler = ClockSampler(gpu_identifier(torch, local))
+    trials, ms, press = timed_steps(s32, args.steps, args.warmup, sampler)
+    ms_max = max_over_ranks(ms)
+    trials_all = sum_over_ranks(trials)
+    value = trials_all / (ms_max / 1e3)
+    clocks = sampler.summary()
+
+    # kernel-level times on the same stream (direct launches with CUDA events)
+    ms_sub, ms_shift, ms_draw = hdmc.hdmc_profile_sweeps(s32.h, 20)
+    hbm_peak, peak_kind = load_peaks()
+    C = s32.C
+    # algorithmic bytes of one sub-sweep launch: every live particle read once
+    # (the halos of the active cells cover the grid) + the active set's
+    # particles written once: 1.25 * N * 8 B (binary32 offsets)
+    bytes_sub = 1.25 * w.N * 8
+    achieved = bytes_sub / (ms_sub / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    loc, cnt = s32.state()
+    info = s32.info()
+    h2d = C * 4 * 8
+    d2h = C * 4 * 8 + 200 * 8
+    e2e_trials, e2e_s = 0, 0.0
+    torch.cuda.synchronize(dev)
+    for k in range(max(1, args.steps)):
+        c0 = int(s32.counters()[0])
+        t0 = time.perf_counter()
+        s32.set_state(loc, cnt, info["origin"], info["sweeps_done"], info["shifts_done"])   # H2D
+        bp, g0, _, _ = one_step(s32)                                                       # D2H histogram
+        loc, cnt = s32.state()                                                              # D2H state
+        t1 = time.perf_counter()
+        info = s32.info()
+        e2e_trials += int(s32.counters()[0]) - c0
+        e2e_s += t1 - t0
+    e2e_s = max_over_ranks(e2e_s)
+    e2e_value = sum_over_ranks(e2e_trials) / e2e_s
+    s32.close()
+
+    # ---- binary64 path on the same workload ----
+    s64 = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, seed, "fp64", device=dev)
+    t64, ms64, _ = timed_steps(s64, args.fp64_steps, 1)
+    ms64 = max_over_ranks(ms64)
+    value64 = sum_over_ranks(t64) / (ms64 / 1e3)
+    ms_sub64, ms_shift64, _ = hdmc.hdmc_profile_sweeps(s64.h, 2)
+    s64.close()
+
+    launches_per_step = KERNELS_PER_SWEEP * SWEEPS_PER_STEP + math.ceil(SWEEPS_PER_STEP / GRAPH_CHUNK) + 1
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "trial moves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "phi": 0.716, "box": [round(w.Lx, 4), round(w.Ly, 4)],
+                   "cells": [s32.mx, s32.my], "d": w.d, "nselect": w.nselect,
+                   "step": "%d sweeps + contact histogram + pressure fit" % SWEEPS_PER_STEP,
+                   "trial_moves_per_step": trials / args.steps,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": "replicas x%d" % world},
+        "e2e": {"value": e2e_value, "unit": "trial moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_subsweep<float>",
+                     "peak_kind": peak_kind, "ms_per_launch": ms_sub,
+                     "algorithmic_bytes_per_launch": bytes_sub},
+        "kernels_ms": {"subsweep_f32": ms_sub, "shift_f32": ms_shift, "draws": ms_draw,
+                       "subsweep_f64": ms_sub64, "shift_f64": ms_shift64},
+        "fp64": {"value": value64, "unit": "trial moves/s", "ms_per_step": ms64 / max(1, args.fp64_steps),
+                 "steps": args.fp64_steps},
+        "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
+        "pressure_betaP_over_rho_last": press[-1] if press else None,
+    }
+    return line
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def oracle_sample(seconds_budget=12.0, threads=None):
+    """The oracle, as it stands, on the bench workload (binary32 mode, all
+    host cores): sweeps + one contact histogram + the pressure fit, until the
+    time budget is used.  Returns (trial moves/s, threads, description)."""
+    import oracle
+    w = workload()
+    nt = oracle.set_threads(threads or (os.cpu_count() or 1))
+    s = oracle.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, oracle.FP32)
+    t0 = time.perf_counter()
+    c0 = int(s.counters()[0])
+    sweeps = 0
+    while True:
+        s.sweep(1)
+        sweeps += 1
+        if time.perf_counter() - t0 > seconds_budget * 0.8:
+            break
+    h = s.histogram()
+    oracle.pressure.pressure(h, 1, w.N, w.Lx * w.Ly)
+    dt = time.perf_counter() - t0
+    trials = int(s.counters()[0]) - c0
+    return trials / dt, nt, "%d sweeps + 1 contact histogram + pressure fit of the N=1048576 workload" % sweeps
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores, same workload."""
+    import oracle
+    w = workload()
+    nt = oracle.set_threads(os.cpu_count() or 1)
+    s = oracle.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, oracle.FP32)
+
+    def step():
+        s.sweep(1)
+        h = s.histogram()
+        oracle.pressure.pressure(h, 1, w.N, w.Lx * w.Ly)
+
+    for _ in range(args.warmup):
+        step()
+    c0 = int(s.counters()[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    trials = int(s.counters()[0]) - c0
+    value = trials / dt
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "trial moves/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "phi": 0.716, "d": w.d, "nselect": w.nselect,
+                   "step": "1 sweep + contact histogram + pressure fit (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "trial moves/s", "cores": nt, "kind": "oracle",
+                         "sample": "%d steps of 1 sweep + contact histogram + pressure fit, N=1048576" % args.steps},
+        "e2e": {"value": value, "unit": "trial moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_hdmc(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            v, nt, sample = oracle_sample()
+            line["cpu_baseline"] = {"value": v, "unit": "trial moves/s", "cores": nt, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

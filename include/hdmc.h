@@ -1,0 +1,182 @@
+/*
+ * hdmc.h -- C ABI of the GB300 hard-disk Monte Carlo library (libhdmc.so).
+ *
+ * The library runs the massively parallel Monte Carlo (MPMC) method of
+ * Anderson, Jankowski, Grubb, Engel and Glotzer, "Massively parallel Monte
+ * Carlo for many-particle simulations on GPUs", J. Comput. Phys. 2013, for N
+ * hard disks of diameter sigma in a periodic Lx x Ly box, on one NVIDIA
+ * GB300 (sm_103a):
+ *   - the box is cut into an mx x my grid of cells of width >= sigma that
+ *     fall into four checkerboard sets (Sec. 2.1, Eq. 1);
+ *   - a sweep shuffles the order of the sets, and for each set lets every
+ *     cell of that set shuffle its disks and make n_M trial translations,
+ *     rejecting moves that leave the cell or overlap a disk of the 3x3
+ *     neighbourhood; it then translates all disks by a random distance
+ *     along a random axis direction (a grid shift), which restores
+ *     ergodicity (Sec. 2.2, Algorithm 1; Algorithms 2 and 4);
+ *   - the pressure comes from the contact value of the pair distribution,
+ *     P* = sigma^2 rho (1 + (pi/2) sigma^2 rho g(sigma+)) (Sec. 4, Eq. P).
+ *
+ * Conventions for every entry point:
+ *   - Return value: HDMC_OK (0) or one of the HDMC_E* codes below; a
+ *     failing call leaves the handle usable unless it returns HDMC_ECUDA.
+ *   - Host pointers are read or written before the call returns; the
+ *     library keeps no reference to them.  Device pointers are named so.
+ *   - Work is enqueued on the handle's CUDA stream (the legacy default
+ *     stream unless hdmc_set_stream was called).  Calls documented as
+ *     "synchronises" wait for that stream; the others return after
+ *     enqueueing.  Errors raised on the device (cell overflow) are reported
+ *     by the next synchronising call.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *
+ * State layout (for hdmc_get_state/hdmc_set_state and the exported
+ * positions): cells are numbered canonically c = cy*mx + cx; each cell has 4
+ * slots (a cell narrower than sqrt(2) sigma holds at most 4 disk centres,
+ * Sec. 3.1, Fig. 3); slot j of cell c holds a disk iff j < count[c]; a
+ * disk's coordinates are stored relative to its cell's lower-left corner
+ * (Sec. 3.1, cell-local frames) and lie in [0,wx) x [0,wy).  Unused slots
+ * read HDMC_EMPTY_SLOT.  Disks carry no identity: slot order is the order
+ * the last shuffle left them in.
+ */
+#ifndef HDMC_H
+#define HDMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define HDMC_OK 0
+#define HDMC_EINVAL 1    /* invalid argument or state */
+#define HDMC_ECUDA 2     /* a CUDA runtime call failed; the handle should be destroyed */
+#define HDMC_EOVERFLOW 3 /* more than 4 disks in one cell */
+#define HDMC_EOVERLAP 4  /* two disks closer than sigma */
+#define HDMC_ETIMEOUT 5  /* a bounded device wait gave up */
+#define HDMC_ENOMEM 6    /* allocation failed or workspace too small */
+
+/* ---- precision of the stored coordinates ---- */
+#define HDMC_FP64 0       /* binary64 cell-local offsets; bit-identical to the serial reference */
+#define HDMC_FP32_LOCAL 1 /* binary32 cell-local offsets (Sec. 5 stores binary32 coordinates) */
+
+#define HDMC_EMPTY_SLOT (-1.0e4)
+#define HDMC_HIST_BINS 200 /* contact histogram: bins of 1e-4 sigma over [sigma, 1.02 sigma) (Sec. 4) */
+
+typedef struct hdmc_handle hdmc_t;
+
+/* Bytes of device memory a handle needs for these parameters (0 if they
+ * are invalid).  Memory is 2 copies of the cell state (mx*my cells of 64 B
+ * for HDMC_FP64, 32 B for HDMC_FP32_LOCAL) plus a few kilobytes of tables. */
+size_t hdmc_workspace_bytes(int64_t N, double Lx, double Ly, double sigma, int precision);
+
+/* Creates a system of N disks (N even, >= 2) placed on a hexagonal lattice
+ * of nx x ny sites (ny even, nx*ny = N, the factorisation whose row spacing
+ * is closest to sqrt(3)/2 of the column spacing), each displaced uniformly
+ * within 0.01 sigma, and binned into the cell grid:
+ *   mx = largest even integer <= Lx/sigma (likewise my), wx = Lx/mx,
+ *   wy = Ly/my; requires mx, my >= 4 and wx, wy < sqrt(2) sigma.
+ * d is the maximum trial displacement (0 < d < min(wx,wy)/2), nselect the
+ * number n_M of trial moves per cell and sub-sweep (1..255), seed the key of
+ * every random stream.  precision is HDMC_FP64 or HDMC_FP32_LOCAL.
+ * dev_workspace: NULL (the library allocates with cudaMalloc and frees in
+ * hdmc_destroy) or a device buffer of at least hdmc_workspace_bytes() bytes,
+ * 256-byte aligned, owned by the caller, which must outlive the handle.
+ * stream: a cudaStream_t or NULL for the legacy default stream.
+ * Errors: HDMC_EINVAL (parameters), HDMC_EOVERLAP / HDMC_EOVERFLOW (start
+ * not legal), HDMC_ENOMEM, HDMC_ECUDA.  *out is NULL on failure.
+ * Synchronises. */
+int hdmc_create(hdmc_t **out, int64_t N, double Lx, double Ly, double sigma, double d, int nselect,
+                uint64_t seed, int precision, void *dev_workspace, size_t workspace_bytes, void *stream);
+
+/* Replaces the configuration by N disks at the host global coordinates
+ * xy[2*i], xy[2*i+1] in [0,Lx] x [0,Ly] (slot order = order of i within a
+ * cell).  Resets the grid origin to 0 but keeps the sweep count and the
+ * counters.  Errors: HDMC_EINVAL (outside the box), HDMC_EOVERFLOW,
+ * HDMC_EOVERLAP; the previous configuration is kept on error.  Synchronises. */
+int hdmc_set_positions(hdmc_t *h, const double *xy);
+
+/* Enqueues n sweeps of Algorithm 1: the set order and the shift come from
+ * the sweep's own random stream, then 4 sub-sweeps (Algorithm 2) and one
+ * cell shift (Algorithm 4).  Sweeps are recorded once into CUDA graphs and
+ * replayed.  Returns after enqueueing. */
+int hdmc_sweep(hdmc_t *h, int64_t n);
+
+/* Enqueues one extra cell shift (Algorithm 4) drawn from the stream of
+ * explicit shifts (independent of the sweeps' streams). */
+int hdmc_shift(hdmc_t *h);
+
+/* Enqueues the contact histogram of the current configuration (ordered
+ * pairs at distance r in [sigma, 1.02 sigma), bins of 1e-4 sigma, Sec. 4)
+ * and adds it to the handle's sample accumulator. */
+int hdmc_sample(hdmc_t *h);
+
+/* Pressure from the accumulated samples (one sample of the current
+ * configuration is taken first if none were): g(R_i) by Eq. gR at the
+ * points R_i of Eq. R, a least-squares polynomial of degree 5 over
+ * (sigma, 1.02 sigma] extrapolated to sigma, and Eq. P.  Outputs (each
+ * nullable): betaP_over_rho = 1 + (pi/2) rho sigma^2 g(sigma+),
+ * g_contact = g(sigma+), hist = the accumulated HDMC_HIST_BINS counts,
+ * n_samples = number of configurations accumulated.  Clears the
+ * accumulator.  Synchronises. */
+int hdmc_pressure(hdmc_t *h, double *betaP_over_rho, double *g_contact, uint64_t *hist, int64_t *n_samples);
+
+/* Global coordinates of every disk into host xy[2N], in canonical (cell,
+ * slot) order: x = O_x + cx*wx + local_x wrapped into [0, mx*wx) (likewise
+ * y), O the accumulated grid origin; cells use the binary32 widths in
+ * HDMC_FP32_LOCAL mode.  cell (nullable, host int32[N]) receives each disk's
+ * canonical cell index.  Synchronises. */
+int hdmc_positions(hdmc_t *h, double *xy, int32_t *cell);
+
+/* Raw state in the canonical layout described above: local[(4c+j)*2 + k]
+ * (host, 8*mx*my doubles; binary32 values widened exactly) and counts[c]
+ * (host, mx*my bytes).  Synchronises. */
+int hdmc_get_state(hdmc_t *h, double *local, uint8_t *counts);
+
+/* Restores a raw state taken by hdmc_get_state together with the origin and
+ * sweep/shift counters returned by hdmc_info, so that a run can resume
+ * bit-identically (the random streams are counter-based).  Values must be
+ * representable in the handle's precision.  Synchronises. */
+int hdmc_set_state(hdmc_t *h, const double *local, const uint8_t *counts, const double origin[2],
+                   uint64_t sweeps_done, uint64_t shifts_done);
+
+/* Cumulative trial counters: out[0] trial moves attempted (n_M per occupied
+ * active cell and sub-sweep), out[1] accepted, out[2] rejected because the
+ * disk would leave its cell, out[3] rejected because of an overlap.
+ * Synchronises. */
+int hdmc_counters(hdmc_t *h, uint64_t out[4]);
+
+/* Geometry and progress: cell grid, cell widths (binary64), sweeps and
+ * explicit shifts done, grid origin (nullable outputs).  Synchronises. */
+int hdmc_info(hdmc_t *h, int32_t *mx, int32_t *my, double *wx, double *wy, uint64_t *sweeps_done,
+              uint64_t *shifts_done, double origin[2]);
+
+/* Changes the maximum trial displacement d (0 < d < min(wx,wy)/2) for the
+ * sweeps enqueued after this call. */
+int hdmc_set_move_size(hdmc_t *h, double d);
+
+/* Uses stream (a cudaStream_t; NULL = legacy default stream) from now on. */
+int hdmc_set_stream(hdmc_t *h, void *stream);
+
+/* Waits for the handle's stream and reports device-side errors. */
+int hdmc_sync(hdmc_t *h);
+
+/* Profiling form of hdmc_sweep: runs n sweeps with the same results, but
+ * launches every kernel directly (no graph) with a CUDA event pair around
+ * it on the handle's stream, and returns the mean device time in
+ * milliseconds of one sub-sweep launch, one cell-shift launch and one
+ * draws launch (each nullable).  Synchronises. */
+int hdmc_profile_sweeps(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift, double *ms_draws);
+
+/* Frees the handle (and the workspace if the library allocated it). */
+void hdmc_destroy(hdmc_t *h);
+
+/* Static description of an error code. */
+const char *hdmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDMC_H */

@@ -1,0 +1,12 @@
+// Binary64 cell-local coordinates (HDMC_FP64).
+#include "hdmc_kernels.cuh"
+
+namespace hdmc {
+void launch_subsweep_f64(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k) {
+    launch_subsweep_t<double>(c, cells, draw, k);
+}
+void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
+    launch_shift_t<double>(c, src, dst, draw);
+}
+void launch_hist_f64(const LaunchCtx& c, const void* cells) { launch_hist_t<double>(c, cells); }
+}  // namespace hdmc

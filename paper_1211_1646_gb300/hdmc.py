@@ -1,0 +1,294 @@
+"""Python binding of libhdmc.so (include/hdmc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all Monte Carlo work runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the workspace) and the CUDA stream.
+If libhdmc.so has not been built, every call raises; there is no CPU path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HDMC_OK, HDMC_EINVAL, HDMC_ECUDA, HDMC_EOVERFLOW, HDMC_EOVERLAP, HDMC_ETIMEOUT, HDMC_ENOMEM = range(7)
+HDMC_FP64, HDMC_FP32_LOCAL = 0, 1
+HDMC_EMPTY_SLOT = -1.0e4
+HDMC_HIST_BINS = 200
+
+_PRECISIONS = {"fp64": HDMC_FP64, "fp32": HDMC_FP32_LOCAL, "fp32_local": HDMC_FP32_LOCAL,
+               HDMC_FP64: HDMC_FP64, HDMC_FP32_LOCAL: HDMC_FP32_LOCAL}
+
+_lib = None
+_vp = ctypes.c_void_p
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+# name -> (restype, argtypes), as declared in include/hdmc.h
+SIGNATURES = {
+    "hdmc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int]),
+    "hdmc_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                   _vp, ctypes.c_size_t, _vp]),
+    "hdmc_set_positions": (ctypes.c_int, [_vp, _f64p]),
+    "hdmc_sweep": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "hdmc_shift": (ctypes.c_int, [_vp]),
+    "hdmc_sample": (ctypes.c_int, [_vp]),
+    "hdmc_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
+    "hdmc_positions": (ctypes.c_int, [_vp, _f64p, _i32p]),
+    "hdmc_get_state": (ctypes.c_int, [_vp, _f64p, _u8p]),
+    "hdmc_set_state": (ctypes.c_int, [_vp, _f64p, _u8p, _f64p, ctypes.c_uint64, ctypes.c_uint64]),
+    "hdmc_counters": (ctypes.c_int, [_vp, _u64p]),
+    "hdmc_info": (ctypes.c_int, [_vp, _i32p, _i32p, _f64p, _f64p, _u64p, _u64p, _f64p]),
+    "hdmc_set_move_size": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "hdmc_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "hdmc_sync": (ctypes.c_int, [_vp]),
+    "hdmc_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p, _f64p]),
+    "hdmc_destroy": (None, [_vp]),
+    "hdmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+class HDMCError(RuntimeError):
+    def __init__(self, code, where):
+        msg = "%s: %s (code %d)" % (where, hdmc_strerror(code) if _lib is not None else "error", code)
+        super().__init__(msg)
+        self.code = code
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libhdmc.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libhdmc.so is not built (%s); run __graft_entry__.build() first" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != HDMC_OK:
+        raise HDMCError(code, where)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _precision(p):
+    try:
+        return _PRECISIONS[p]
+    except KeyError:
+        raise ValueError("precision must be 'fp64' or 'fp32'") from None
+
+
+# ---- one Python function per C entry point ----------------------------------------
+
+def hdmc_strerror(code):
+    return lib().hdmc_strerror(code).decode()
+
+
+def hdmc_workspace_bytes(N, Lx, Ly, sigma, precision):
+    return int(lib().hdmc_workspace_bytes(N, Lx, Ly, sigma, _precision(precision)))
+
+
+def hdmc_create(N, Lx, Ly, sigma, d, nselect, seed, precision, dev_workspace=None, workspace_bytes=0,
+                stream=None):
+    h = _vp()
+    _check(lib().hdmc_create(ctypes.byref(h), N, Lx, Ly, sigma, d, nselect, seed & 0xFFFFFFFFFFFFFFFF,
+                             _precision(precision), dev_workspace, workspace_bytes, stream), "hdmc_create")
+    return h
+
+
+def hdmc_set_positions(h, xy):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    _check(lib().hdmc_set_positions(h, _p(xy, _f64p)), "hdmc_set_positions")
+
+
+def hdmc_sweep(h, n):
+    _check(lib().hdmc_sweep(h, n), "hdmc_sweep")
+
+
+def hdmc_shift(h):
+    _check(lib().hdmc_shift(h), "hdmc_shift")
+
+
+def hdmc_sample(h):
+    _check(lib().hdmc_sample(h), "hdmc_sample")
+
+
+def hdmc_pressure(h):
+    """Returns (betaP_over_rho, g_contact, hist[200] uint64, n_samples)."""
+    bp, g0 = ctypes.c_double(), ctypes.c_double()
+    ns = ctypes.c_int64()
+    hist = np.zeros(HDMC_HIST_BINS, dtype=np.uint64)
+    _check(lib().hdmc_pressure(h, ctypes.byref(bp), ctypes.byref(g0), _p(hist, _u64p), ctypes.byref(ns)),
+           "hdmc_pressure")
+    return bp.value, g0.value, hist, ns.value
+
+
+def hdmc_positions(h, N):
+    xy = np.zeros(2 * N, dtype=np.float64)
+    cell = np.zeros(N, dtype=np.int32)
+    _check(lib().hdmc_positions(h, _p(xy, _f64p), _p(cell, _i32p)), "hdmc_positions")
+    return xy.reshape(N, 2), cell
+
+
+def hdmc_get_state(h, C):
+    loc = np.zeros(8 * C, dtype=np.float64)
+    cnt = np.zeros(C, dtype=np.uint8)
+    _check(lib().hdmc_get_state(h, _p(loc, _f64p), _p(cnt, _u8p)), "hdmc_get_state")
+    return loc.reshape(C, 4, 2), cnt
+
+
+def hdmc_set_state(h, local, counts, origin, sweeps_done, shifts_done):
+    loc = np.ascontiguousarray(local, dtype=np.float64).reshape(-1)
+    cnt = np.ascontiguousarray(counts, dtype=np.uint8)
+    org = np.ascontiguousarray(origin, dtype=np.float64)
+    _check(lib().hdmc_set_state(h, _p(loc, _f64p), _p(cnt, _u8p), _p(org, _f64p), sweeps_done, shifts_done),
+           "hdmc_set_state")
+
+
+def hdmc_counters(h):
+    out = np.zeros(4, dtype=np.uint64)
+    _check(lib().hdmc_counters(h, _p(out, _u64p)), "hdmc_counters")
+    return out
+
+
+def hdmc_info(h):
+    mx, my = ctypes.c_int32(), ctypes.c_int32()
+    wx, wy = ctypes.c_double(), ctypes.c_double()
+    sw, sh = ctypes.c_uint64(), ctypes.c_uint64()
+    org = np.zeros(2, dtype=np.float64)
+    _check(lib().hdmc_info(h, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(wx), ctypes.byref(wy),
+                           ctypes.byref(sw), ctypes.byref(sh), _p(org, _f64p)), "hdmc_info")
+    return {"mx": mx.value, "my": my.value, "wx": wx.value, "wy": wy.value, "sweeps_done": sw.value,
+            "shifts_done": sh.value, "origin": org}
+
+
+def hdmc_set_move_size(h, d):
+    _check(lib().hdmc_set_move_size(h, d), "hdmc_set_move_size")
+
+
+def hdmc_set_stream(h, stream):
+    _check(lib().hdmc_set_stream(h, stream), "hdmc_set_stream")
+
+
+def hdmc_sync(h):
+    _check(lib().hdmc_sync(h), "hdmc_sync")
+
+
+def hdmc_profile_sweeps(h, n):
+    """Returns mean ms per (sub-sweep, shift, draws) launch over n directly launched sweeps."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().hdmc_profile_sweeps(h, n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "hdmc_profile_sweeps")
+    return a.value, b.value, c.value
+
+
+def hdmc_destroy(h):
+    if h is not None and h.value:
+        lib().hdmc_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+class System:
+    """One hard-disk system on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor (PyTorch's caching allocator
+    owns the memory) and work goes to torch's current stream unless a stream
+    is given.  If xy is given, the lattice start is replaced by those global
+    positions.
+    """
+
+    def __init__(self, N, Lx, Ly, sigma=1.0, d=0.1, nselect=4, seed=1, precision="fp32", xy=None,
+                 stream=None, device=None):
+        import torch
+
+        self.N, self.Lx, self.Ly, self.sigma = N, Lx, Ly, sigma
+        self.precision = _precision(precision)
+        nbytes = hdmc_workspace_bytes(N, Lx, Ly, sigma, self.precision)
+        if nbytes == 0:
+            raise HDMCError(HDMC_EINVAL, "hdmc_workspace_bytes")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self._ws.data_ptr()
+        ptr = (base + 255) // 256 * 256
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        self._stream = stream
+        self.h = None
+        self.h = hdmc_create(N, Lx, Ly, sigma, d, nselect, seed, self.precision, ptr, nbytes, stream)
+        info = hdmc_info(self.h)
+        self.mx, self.my, self.wx, self.wy = info["mx"], info["my"], info["wx"], info["wy"]
+        self.C = self.mx * self.my
+        if xy is not None:
+            hdmc_set_positions(self.h, xy)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            hdmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        hdmc_sweep(self.h, n)
+
+    def shift(self):
+        hdmc_shift(self.h)
+
+    def sample(self):
+        hdmc_sample(self.h)
+
+    def pressure(self):
+        return hdmc_pressure(self.h)
+
+    def positions(self):
+        return hdmc_positions(self.h, self.N)[0]
+
+    def state(self):
+        return hdmc_get_state(self.h, self.C)
+
+    def set_state(self, local, counts, origin, sweeps_done, shifts_done):
+        hdmc_set_state(self.h, local, counts, origin, sweeps_done, shifts_done)
+
+    def counters(self):
+        return hdmc_counters(self.h)
+
+    def info(self):
+        return hdmc_info(self.h)
+
+    def origin(self):
+        return hdmc_info(self.h)["origin"]
+
+    def set_move_size(self, d):
+        hdmc_set_move_size(self.h, d)
+
+    def sync(self):
+        hdmc_sync(self.h)
+
+    def box(self):
+        if self.precision == HDMC_FP64:
+            return self.Lx, self.Ly
+        return self.mx * float(np.float32(self.wx)), self.my * float(np.float32(self.wy))

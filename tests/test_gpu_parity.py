@@ -1,0 +1,260 @@
+"""Parity of the CUDA library (through its C ABI) with the oracle.
+
+Both paths are deterministic functions of (configuration, seed, sweep index):
+the binary64 path must agree with the oracle's binary64 mode bit for bit,
+and the binary32 path with the oracle's binary32 mode bit for bit --
+positions, cell counts, slot order, trial counters, grid origin and the
+contact histogram.  Sizes span several thread blocks with ragged tails;
+the largest cases are the N = 1M and N = 4M workloads of the benchmark,
+checked after a few sweeps against the (multi-threaded) oracle.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import pressure as P
+from paper_1211_1646_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp64": O.FP64, "fp32": O.FP32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1211_1646_gb300 import build
+    build.build()
+    O.set_threads(os.cpu_count() or 1)
+    yield
+    O.set_threads(1)
+
+
+def _pair(w, prec, seed=None, d=None, nsel=None, xy=None):
+    from paper_1211_1646_gb300 import hdmc
+    seed = w.seed if seed is None else seed
+    d = w.d if d is None else d
+    nsel = w.nselect if nsel is None else nsel
+    g = hdmc.System(w.N, w.Lx, w.Ly, 1.0, d, nsel, seed, prec, xy=xy)
+    r = O.System(w.N, w.Lx, w.Ly, 1.0, d, nsel, seed, PREC[prec], xy=xy)
+    return g, r
+
+
+def _same(g, r, what=""):
+    lg, cg = g.state()
+    lr, cr = r.state()
+    assert np.array_equal(cg, cr), "counts differ " + what
+    bad = np.argwhere(lg != lr)
+    assert bad.size == 0, "positions differ at %s %s" % (bad[:4].tolist(), what)
+    assert np.array_equal(g.counters(), r.counters()), "counters differ " + what
+    assert np.array_equal(g.origin(), r.origin()), "origin differs " + what
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_start_configuration(prec):
+    for w in (W.n1024_phi070(), W.n65536_phi070()):
+        g, r = _pair(w, prec)
+        _same(g, r, "after create")
+        assert np.array_equal(g.positions(), r.positions())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_n1024_200_sweeps(prec):
+    w = W.n1024_phi070()
+    g, r = _pair(w, prec)
+    for k in range(4):
+        g.sweep(50)
+        r.sweep(50)
+        _same(g, r, "after %d sweeps" % (50 * (k + 1)))
+    assert g.info()["sweeps_done"] == 200
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_n65536_20_sweeps(prec):
+    w = W.n65536_phi070()
+    g, r = _pair(w, prec)
+    g.sweep(20)
+    r.sweep(20)
+    _same(g, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_n1m_hex_phi0716(prec):
+    w = W.n1m_phi0716(prec)
+    g, r = _pair(w, prec)
+    g.sweep(3)
+    r.sweep(3)
+    _same(g, r)
+
+
+def test_n4m_phi0716_fp32():
+    w = W.n4m(0.716, "fp32")
+    g, r = _pair(w, "fp32")
+    g.sweep(2)
+    r.sweep(2)
+    _same(g, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_grid_and_nselect(prec):
+    # 36 x 22 cells: set rows of 18 cells (not a multiple of 32), 11 set rows
+    # (not a multiple of 4); odd n_M
+    Lx, Ly = 37.3, 23.9
+    N = 2 * 300
+    w = W.Workload("ragged", N, Lx, Ly, 0.2, 7, 99, 0)
+    g, r = _pair(w, prec)
+    g.sweep(65)      # one full 64-sweep graph plus a 1-sweep graph
+    r.sweep(65)
+    _same(g, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_systems(prec):
+    for N, L in ((2, 4.0), (16, 8.5)):
+        w = W.Workload("tiny", N, L, L, 0.3, 4, 5, 0)
+        g, r = _pair(w, prec)
+        g.sweep(130)
+        r.sweep(130)
+        _same(g, r, "N=%d" % N)
+
+
+def test_chunking_does_not_change_results():
+    from paper_1211_1646_gb300 import hdmc
+    w = W.n1024_phi070()
+    a = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 3, "fp32")
+    b = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 3, "fp32")
+    a.sweep(130)
+    for _ in range(130):
+        b.sweep(1)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    assert np.array_equal(a.counters(), b.counters())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_explicit_shift(prec):
+    w = W.n1024_phi070()
+    g, r = _pair(w, prec)
+    g.sweep(7)
+    r.sweep(7)
+    for _ in range(9):
+        g.shift()
+        r.shift()
+    _same(g, r)
+    g.sweep(3)
+    r.sweep(3)
+    _same(g, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_contact_histogram_and_pressure(prec):
+    w = W.n65536_phi070()
+    g, r = _pair(w, prec)
+    hr = np.zeros(200, dtype=np.uint64)
+    for k in range(3):
+        g.sweep(10)
+        r.sweep(10)
+        g.sample()
+        hr += r.histogram()
+    bp, g0, hist, ns = g.pressure()
+    assert ns == 3
+    assert np.array_equal(hist, hr)
+    bp_ref, g0_ref, _ = P.pressure(hr, 3, w.N, w.Lx * w.Ly)
+    assert abs(g0 - g0_ref) < 1e-9 * abs(g0_ref)
+    assert abs(bp - bp_ref) < 1e-9 * abs(bp_ref)
+    # the accumulator was cleared: the next call samples the current state
+    bp2, _, hist2, ns2 = g.pressure()
+    assert ns2 == 1 and np.array_equal(hist2, r.histogram())
+
+
+def test_histogram_at_1m():
+    w = W.n1m_phi0716("fp32")
+    g, r = _pair(w, "fp32")
+    g.sweep(2)
+    r.sweep(2)
+    _, _, hist, _ = g.pressure()
+    assert np.array_equal(hist, r.histogram())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_set_positions_and_errors(prec):
+    from paper_1211_1646_gb300 import hdmc
+    L = 20.0
+    w = W.Workload("rsa", 40, L, L, 0.25, 4, 8, 0)
+    rng = np.random.default_rng(5)
+    pts = []
+    while len(pts) < 40:
+        p = rng.uniform(0, L, 2)
+        if all(math.hypot(*((p - q) - L * np.round((p - q) / L))) > 1.05 for q in pts):
+            pts.append(p)
+    xy = np.array(pts)
+    g, r = _pair(w, prec, xy=xy)
+    _same(g, r, "after set_positions")
+    g.sweep(40)
+    r.sweep(40)
+    _same(g, r)
+    bad = xy.copy()
+    bad[1] = bad[0] + [0.5, 0.0]
+    bad[1] %= L
+    with pytest.raises(hdmc.HDMCError) as e:
+        g.sys_set = hdmc.hdmc_set_positions(g.h, bad)
+    assert e.value.code == hdmc.HDMC_EOVERLAP
+    _same(g, r, "state kept after a rejected set_positions")
+    with pytest.raises(hdmc.HDMCError) as e:
+        hdmc.System(40, L, L, 1.0, 0.9, 4, 1, prec)
+    assert e.value.code == hdmc.HDMC_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bit_identical(prec):
+    from paper_1211_1646_gb300 import hdmc
+    w = W.n1024_phi070()
+    a = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 12, prec)
+    a.sweep(100)
+    loc, cnt = a.state()
+    info = a.info()
+    b = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 12, prec)
+    b.set_state(loc, cnt, info["origin"], info["sweeps_done"], info["shifts_done"])
+    a.sweep(100)
+    b.sweep(100)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    assert np.array_equal(a.positions(), b.positions())
+
+
+def test_torch_side_stream():
+    import torch
+    from paper_1211_1646_gb300 import hdmc
+    w = W.n1024_phi070()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 1, "fp64")
+        g.sweep(30)
+    r = O.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 1, O.FP64)
+    r.sweep(30)
+    _same(g, r)
+
+
+def test_invariants_on_gpu_fp32_long_run():
+    # 2000 sweeps at phi = 0.716: particle count, n <= 4, containment, no overlap
+    from paper_1211_1646_gb300 import hdmc
+    w = W.n65536_phi070()
+    Lx, Ly = W.hex_box(256, 256, 0.716)
+    g = hdmc.System(65536, Lx, Ly, 1.0, 0.08, 4, 77, "fp32")
+    g.sweep(2000)
+    loc, cnt = g.state()
+    assert int(cnt.sum()) == 65536 and cnt.max() <= 4
+    occ = np.arange(4)[None, :] < cnt[:, None]
+    wx32 = float(np.float32(g.wx))
+    wy32 = float(np.float32(g.wy))
+    assert np.all((loc[..., 0][occ] >= 0) & (loc[..., 0][occ] < wx32))
+    assert np.all((loc[..., 1][occ] >= 0) & (loc[..., 1][occ] < wy32))
+    from scipy.spatial import cKDTree
+    bx, by = g.box()
+    xy = g.positions()
+    assert xy.min() >= 0 and xy[:, 0].max() < bx and xy[:, 1].max() < by
+    pairs = cKDTree(xy, boxsize=[bx, by]).query_pairs(1.0 - 1e-6)
+    assert len(pairs) == 0
