@@ -45,7 +45,25 @@ def parse():
     ap.add_argument("--impl", default="hdmc", choices=["hdmc", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the binary64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m"],
+                    help="run a short fixed workload for an ncu capture and exit (no timing)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
+
+
+def ncu_case(args):
+    """A few sweeps and one contact histogram of the N=1M (74 MB of binary32
+    state) or N=4M (294 MB, larger than L2) phi=0.716 workload."""
+    import torch
+    from paper_1211_1646_gb300 import build, hdmc, workloads
+    build.build()
+    w = workloads.n1m_phi0716() if args.ncu_case == "n1m" else workloads.n4m(0.716)
+    s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, args.precision)
+    s.sweep(3)
+    s.sample()
+    s.pressure()
+    torch.cuda.synchronize()
+    print("ncu case %s %s done: counters %s" % (w.name, args.precision, list(s.counters())))
 
 
 def workload():
@@ -348,6 +366,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

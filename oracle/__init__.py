@@ -45,7 +45,6 @@ def lib():
                                         ctypes.c_int64, _u32p]),
             "orc_lemire_exhaustive": (None, [ctypes.c_uint32, _u64p]),
             "orc_sym52": (ctypes.c_double, [ctypes.c_uint32, ctypes.c_uint32]),
-            "orc_sym23": (ctypes.c_float, [ctypes.c_uint32]),
             "orc_grid": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _i32p, _i32p,
                                         _f64p, _f64p]),
             "orc_lattice_shape": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _i64p, _i64p]),
@@ -78,8 +77,12 @@ def lib():
             "orc_set_threads": (ctypes.c_int, [ctypes.c_int]),
             "orc_displacements": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int64, _f64p]),
-            "orc_shuffles": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+            "orc_shuffles": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int64, _i32p]),
+            "orc_lemire21_exhaustive": (None, [ctypes.c_uint32, _u64p]),
+            "orc_sym21": (ctypes.c_float, [ctypes.c_uint32]),
+            "orc_fields21": (None, [_u32p, _u32p]),
+            "orc_decode_perm": (None, [ctypes.c_int, ctypes.c_uint32, _i32p]),
             "orc_visit_sequence": (None, [ctypes.c_int, ctypes.c_int, _i32p]),
             "orc_local_overlaps": (ctypes.c_int, [vp]),
         }
@@ -171,11 +174,30 @@ def displacements(seed, sweep, Q, t, precision, ncells):
     return uv.reshape(ncells, 2)
 
 
-def shuffles(seed, sweep, Q, n, ncells):
-    """Fisher-Yates orders of n slots for cells 0..ncells-1 (perm[j] = old slot now at j)."""
+def shuffles(seed, sweep, Q, n, ncells, precision=FP64):
+    """Shuffle orders of n slots for cells 0..ncells-1 (perm[j] = old slot now at j)."""
     out = np.zeros(4 * ncells, dtype=np.int32)
-    lib().orc_shuffles(seed, sweep, Q, n, ncells, _p(out, _i32p))
+    lib().orc_shuffles(seed, sweep, Q, n, precision, ncells, _p(out, _i32p))
     return out.reshape(ncells, 4)[:, :n]
+
+
+def lemire21_exhaustive(rng):
+    out = np.zeros(rng, dtype=np.uint64)
+    lib().orc_lemire21_exhaustive(rng, _p(out, _u64p))
+    return out
+
+
+def fields21(words):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    f = np.zeros(6, dtype=np.uint32)
+    lib().orc_fields21(_p(w, _u32p), _p(f, _u32p))
+    return f
+
+
+def decode_perm(n, k):
+    out = np.zeros(4, dtype=np.int32)
+    lib().orc_decode_perm(n, k, _p(out, _i32p))
+    return out[:n]
 
 
 def visit_sequence(n, nsel):

@@ -146,14 +146,6 @@ static double sym52(uint32_t hi, uint32_t lo)
     return (double)m * 0x1p-52;
 }
 
-/* Symmetric binary32 variate from the top 23 bits of one word. */
-static float sym23(uint32_t w)
-{
-    uint32_t k = w >> 9;
-    int32_t m = (int32_t)(2 * k + 1) - (1 << 23);
-    return (float)m * 0x1p-23f;
-}
-
 /* Uniform binary64 in [0,1) with 53 random bits. */
 static double unif53(uint32_t hi, uint32_t lo)
 {
@@ -205,7 +197,6 @@ void orc_lemire_exhaustive(uint32_t range, uint64_t *counts)
 }
 
 double orc_sym52(uint32_t hi, uint32_t lo) { return sym52(hi, lo); }
-float orc_sym23(uint32_t w) { return sym23(w); }
 
 /* ------------------------------------------------------------------------ */
 /* System state                                                              */
@@ -233,6 +224,14 @@ typedef struct oracle {
 
 static double prev_double(double w) { return nextafter(w, 0.0); }
 static float prev_float(float w) { return nextafterf(w, 0.0f); }
+
+/* binary32 overlap predicate: dx^2 + dy^2 < sigma^2 evaluated as
+ * fma(dx, dx, fma(dy, dy, -sigma^2)) < 0 (two roundings).  The binary64
+ * predicate is dx*dx + dy*dy < sigma^2 with three roundings. */
+static int overlap32(float dx, float dy, float sig2)
+{
+    return fmaf(dx, dx, fmaf(dy, dy, -sig2)) < 0.0f;
+}
 
 /* Grid rule: mx = largest even integer <= Lx/sigma, likewise my. */
 static int grid_size(double L, double sigma)
@@ -349,7 +348,7 @@ static int64_t count_overlaps_local(const oracle_t *o)
                                 float ex = (float)qx + (float)dx * o->wxf;
                                 float ey = (float)qy + (float)dy * o->wyf;
                                 float ddx = (float)px - ex, ddy = (float)py - ey;
-                                if (fmaf(ddx, ddx, ddy * ddy) < (float)(o->sigma * o->sigma)) bad++;
+                                if (overlap32(ddx, ddy, (float)(o->sigma * o->sigma))) bad++;
                             }
                         }
                     }
@@ -527,68 +526,178 @@ void orc_sweep_draws(uint64_t seed, uint32_t sweep, double wx, double wy, int32_
 
 /* ------------------------------------------------------------------------ */
 /* Per-cell random draws of a sub-sweep (Alg. 1 lines 5 and 8).              */
+/*                                                                          */
+/* One cell update (sweep s, set Q, canonical cell c) reads its trial       */
+/* stream T = (s, c, (1<<28)|(Q<<24)) and, for binary64 shuffles or a      */
+/* rejected binary32 shuffle draw, its shuffle stream                      */
+/* S = (s, c, (0<<28)|(Q<<24)).  The draws do not depend on positions, so  */
+/* they are all taken before the trials.                                    */
+/*  - Shuffle (n >= 2): one integer k uniform in [0, n!) decoded as the    */
+/*    Fisher-Yates swap sequence (mixed radix), i.e. a uniform random      */
+/*    permutation of the cell's n disks.                                   */
+/*  - Directions: attempts (u,v) uniform in (-1,1)^2, kept when inside the */
+/*    unit disk; trial t uses the t-th kept attempt.                       */
+/* binary64: k by 32-bit Lemire on the words of S; attempt a = block a of T */
+/*   with u = sym52(w0,w1), v = sym52(w2,w3), kept when u*u + v*v < 1.      */
+/* binary32: block b of T is cut into six 21-bit fields; k by 21-bit        */
+/*   Lemire on field 0 of block 0 (if rejected: 32-bit Lemire on S); the   */
+/*   attempts are the field pairs (2,3),(4,5) of block 0, then (0,1),(2,3), */
+/*   (4,5) of blocks 1, 2, ...; u = sym21, kept when fmaf(u,u,v*v) < 1.    */
 /* ------------------------------------------------------------------------ */
 
-/* Fisher-Yates shuffle of slots 0..n-1 (Durstenfeld): for j = n-1 down to 1
- * swap positions j and k_j, k_j uniform in [0, j].  On return perm[j] is the
- * old slot that now sits in slot j. */
-static void shuffle_order(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int perm[4])
+static const uint32_t kFactorial[5] = {1u, 1u, 2u, 6u, 24u};
+
+/* Field j (0..5) = bits [21j, 21j+21) of w0 + 2^32 w1 + 2^64 w2 + 2^96 w3. */
+static void fields21(const uint32_t w[4], uint32_t f[6])
 {
-    stream_t s;
-    stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | ((uint32_t)Q << 24));
+    for (int j = 0; j < 6; ++j) {
+        int bit = 21 * j, word = bit / 32;
+        uint64_t both = (uint64_t)w[word];
+        if (word + 1 < 4) both |= (uint64_t)w[word + 1] << 32;
+        f[j] = (uint32_t)((both >> (bit % 32)) & 0x1FFFFFu);
+    }
+}
+
+/* Lemire's method on a 21-bit field: value floor(f*range / 2^21), rejected
+ * when the low 21 bits of f*range fall below 2^21 mod range. */
+static int lemire21(uint32_t f, uint32_t range, uint32_t *value)
+{
+    uint32_t threshold = (1u << 21) % range;
+    uint32_t m = f * range;
+    *value = m >> 21;
+    return (m & 0x1FFFFFu) >= threshold;
+}
+
+/* Odd multiples of 2^-21 in (-1,1) from a 21-bit field. */
+static float sym21(uint32_t f)
+{
+    int32_t m = (int32_t)(2 * f + 1) - (1 << 21);
+    return (float)m * 0x1p-21f;
+}
+
+/* Fisher-Yates decode of k in [0, n!): for j = n-1 down to 1 swap slots j and
+ * k mod (j+1), then k /= (j+1).  perm[j] = old slot that now sits in slot j. */
+static void decode_perm(int n, uint32_t k, int perm[4])
+{
     for (int j = 0; j < 4; ++j) perm[j] = j;
     for (int j = n - 1; j >= 1; --j) {
-        int k = (int)stream_bounded(&s, (uint32_t)(j + 1));
-        int t = perm[j]; perm[j] = perm[k]; perm[k] = t;
+        int r = (int)(k % (uint32_t)(j + 1));
+        k /= (uint32_t)(j + 1);
+        int t = perm[j]; perm[j] = perm[r]; perm[r] = t;
     }
 }
 
-/* Trial displacement direction (u,v), uniform over the unit disk by
- * rejection: binary64 mode takes 4 words per attempt. */
-static void displacement64(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int t, double *u, double *v)
+static void philox_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t b, uint32_t w[4])
 {
-    stream_t s;
-    stream_open(&s, seed, sweep, cell, (DOM_TRIAL << 28) | ((uint32_t)Q << 24) | (uint32_t)t);
-    do {
-        uint32_t a = stream_word(&s), b = stream_word(&s), e = stream_word(&s), f = stream_word(&s);
-        *u = sym52(a, b);
-        *v = sym52(e, f);
-    } while (!(*u * *u + *v * *v < 1.0));
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {c0, c1, c2, b};
+    orc_philox(ctr, key, w);
 }
 
-/* binary32 mode: 2 words per attempt; u^2 + v^2 evaluated as fmaf(u,u,v*v). */
-static void displacement32(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int t, float *u, float *v)
+/* binary64 draws of one cell update. */
+static void cell_draws64(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
+                         int perm[4], double *U, double *V)
 {
-    stream_t s;
-    stream_open(&s, seed, sweep, cell, (DOM_TRIAL << 28) | ((uint32_t)Q << 24) | (uint32_t)t);
-    do {
-        uint32_t a = stream_word(&s), b = stream_word(&s);
-        *u = sym23(a);
-        *v = sym23(b);
-    } while (!(fmaf(*u, *u, *v * *v) < 1.0f));
+    const uint32_t setbits = (uint32_t)Q << 24;
+    for (int j = 0; j < 4; ++j) perm[j] = j;
+    if (shuffle && n >= 2) {
+        stream_t s;
+        stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | setbits);
+        decode_perm(n, stream_bounded(&s, kFactorial[n]), perm);
+    }
+    uint32_t block = 0;
+    for (int t = 0; t < nsel;) {
+        uint32_t w[4];
+        philox_block(seed, sweep, cell, (DOM_TRIAL << 28) | setbits, block++, w);
+        double u = sym52(w[0], w[1]), v = sym52(w[2], w[3]);
+        if (u * u + v * v < 1.0) { U[t] = u; V[t] = v; ++t; }
+    }
 }
 
-/* Test hooks. */
+/* binary32 draws of one cell update. */
+static void cell_draws32(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
+                         int perm[4], float *U, float *V)
+{
+    const uint32_t setbits = (uint32_t)Q << 24;
+    uint32_t w[4], f[6];
+    philox_block(seed, sweep, cell, (DOM_TRIAL << 28) | setbits, 0, w);
+    fields21(w, f);
+    for (int j = 0; j < 4; ++j) perm[j] = j;
+    if (shuffle && n >= 2) {
+        uint32_t k;
+        if (!lemire21(f[0], kFactorial[n], &k)) {
+            stream_t s;
+            stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | setbits);
+            k = stream_bounded(&s, kFactorial[n]);
+        }
+        decode_perm(n, k, perm);
+    }
+    uint32_t block = 0;
+    int pair = 1;
+    for (int t = 0; t < nsel;) {
+        if (pair == 3) {
+            philox_block(seed, sweep, cell, (DOM_TRIAL << 28) | setbits, ++block, w);
+            fields21(w, f);
+            pair = 0;
+        }
+        float u = sym21(f[2 * pair]), v = sym21(f[2 * pair + 1]);
+        ++pair;
+        if (fmaf(u, u, v * v) < 1.0f) { U[t] = u; V[t] = v; ++t; }
+    }
+}
+
+/* Test hooks: direction of trial t (shuffle off, so independent of n) and
+ * the permutation of an n-disk cell, for cells 0..ncells-1. */
 void orc_displacements(uint64_t seed, uint32_t sweep, int Q, int t, int prec, int64_t ncells, double *uv)
 {
+    int perm[4];
+    double *U = (double *)malloc(sizeof(double) * (size_t)(t + 1));
+    double *V = (double *)malloc(sizeof(double) * (size_t)(t + 1));
+    float *Uf = (float *)malloc(sizeof(float) * (size_t)(t + 1));
+    float *Vf = (float *)malloc(sizeof(float) * (size_t)(t + 1));
     for (int64_t c = 0; c < ncells; ++c) {
         if (prec == 0) {
-            displacement64(seed, sweep, (uint32_t)c, Q, t, &uv[2 * c], &uv[2 * c + 1]);
+            cell_draws64(seed, sweep, (uint32_t)c, Q, 1, 0, t + 1, perm, U, V);
+            uv[2 * c] = U[t]; uv[2 * c + 1] = V[t];
         } else {
-            float u, v;
-            displacement32(seed, sweep, (uint32_t)c, Q, t, &u, &v);
-            uv[2 * c] = u; uv[2 * c + 1] = v;
+            cell_draws32(seed, sweep, (uint32_t)c, Q, 1, 0, t + 1, perm, Uf, Vf);
+            uv[2 * c] = Uf[t]; uv[2 * c + 1] = Vf[t];
         }
+    }
+    free(U); free(V); free(Uf); free(Vf);
+}
+
+void orc_shuffles(uint64_t seed, uint32_t sweep, int Q, int n, int prec, int64_t ncells, int32_t *perms)
+{
+    double U[1], V[1];
+    float Uf[1], Vf[1];
+    for (int64_t c = 0; c < ncells; ++c) {
+        int p[4];
+        if (prec == 0) cell_draws64(seed, sweep, (uint32_t)c, Q, n, 1, 1, p, U, V);
+        else cell_draws32(seed, sweep, (uint32_t)c, Q, n, 1, 1, p, Uf, Vf);
+        for (int j = 0; j < 4; ++j) perms[4 * c + j] = p[j];
     }
 }
 
-void orc_shuffles(uint64_t seed, uint32_t sweep, int Q, int n, int64_t ncells, int32_t *perms)
+/* Exhaustive 21-bit Lemire counts (range <= 24): counts[v] = #fields -> v. */
+void orc_lemire21_exhaustive(uint32_t range, uint64_t *counts)
 {
-    for (int64_t c = 0; c < ncells; ++c) {
-        int p[4];
-        shuffle_order(seed, sweep, (uint32_t)c, Q, n, p);
-        for (int j = 0; j < 4; ++j) perms[4 * c + j] = p[j];
+    memset(counts, 0, sizeof(uint64_t) * range);
+    for (uint32_t f = 0; f < (1u << 21); ++f) {
+        uint32_t v;
+        if (lemire21(f, range, &v)) counts[v] += 1;
     }
+}
+
+float orc_sym21(uint32_t f) { return sym21(f); }
+
+void orc_fields21(const uint32_t w[4], uint32_t f[6]) { fields21(w, f); }
+
+void orc_decode_perm(int n, uint32_t k, int32_t out[4])
+{
+    int p[4];
+    decode_perm(n, k, p);
+    for (int j = 0; j < 4; ++j) out[j] = p[j];
 }
 
 /* Slot visited by trial t of a cell holding n disks: t mod n (Alg. 1 line 7). */
@@ -608,21 +717,18 @@ static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
     int n = o->n[c];
     if (n == 0) return;
     double *X = o->X + 4 * c, *Y = o->Y + 4 * c;
-    /* shuffle the cell's particles (Fisher-Yates) */
-    if (o->shuffle_particles && n >= 2) {
-        int perm[4];
-        shuffle_order(o->seed, sweep, (uint32_t)c, Q, n, perm);
-        double tx[4], ty[4];
-        for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
-        for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
-    }
+    int perm[4];
+    double U[256], V[256];
+    cell_draws64(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, perm, U, V);
+    /* shuffle the cell's particles (Alg. 1 line 5) */
+    double tx[4], ty[4];
+    for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
+    for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
     const double sig2 = o->sigma * o->sigma;
     for (int t = 0; t < o->nsel; ++t) {
         int i = visit_slot(t, n);
-        double u, v;
-        displacement64(o->seed, sweep, (uint32_t)c, Q, t, &u, &v);
-        double nx = X[i] + o->d * u;
-        double ny = Y[i] + o->d * v;
+        double nx = X[i] + o->d * U[t];
+        double ny = Y[i] + o->d * V[t];
         acc[0]++;
         if (!(nx >= 0.0 && nx < o->wx && ny >= 0.0 && ny < o->wy)) { acc[2]++; continue; }
         int overlap = 0;
@@ -656,28 +762,25 @@ static void cell_update32(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
     int n = o->n[c];
     if (n == 0) return;
     float *X = o->Xf + 4 * c, *Y = o->Yf + 4 * c;
-    if (o->shuffle_particles && n >= 2) {
-        int perm[4];
-        shuffle_order(o->seed, sweep, (uint32_t)c, Q, n, perm);
-        float tx[4], ty[4];
-        for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
-        for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
-    }
+    int perm[4];
+    float U[256], V[256];
+    cell_draws32(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, perm, U, V);
+    float tx[4], ty[4];
+    for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
+    for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
     const float sig2 = (float)(o->sigma * o->sigma);
     const float df = (float)o->d;
     for (int t = 0; t < o->nsel; ++t) {
         int i = visit_slot(t, n);
-        float u, v;
-        displacement32(o->seed, sweep, (uint32_t)c, Q, t, &u, &v);
-        float nx = fmaf(df, u, X[i]);
-        float ny = fmaf(df, v, Y[i]);
+        float nx = fmaf(df, U[t], X[i]);
+        float ny = fmaf(df, V[t], Y[i]);
         acc[0]++;
         if (!(nx >= 0.0f && nx < o->wxf && ny >= 0.0f && ny < o->wyf)) { acc[2]++; continue; }
         int overlap = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
             float ddx = nx - X[j], ddy = ny - Y[j];
-            if (fmaf(ddx, ddx, ddy * ddy) < sig2) overlap = 1;
+            if (overlap32(ddx, ddy, sig2)) overlap = 1;
         }
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
@@ -688,7 +791,7 @@ static void cell_update32(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
                 for (int j = 0; j < o->n[nc]; ++j) {
                     float ex = o->Xf[4 * nc + j] + sx, ey = o->Yf[4 * nc + j] + sy;
                     float ddx = nx - ex, ddy = ny - ey;
-                    if (fmaf(ddx, ddx, ddy * ddy) < sig2) overlap = 1;
+                    if (overlap32(ddx, ddy, sig2)) overlap = 1;
                 }
             }
         if (overlap) { acc[3]++; continue; }

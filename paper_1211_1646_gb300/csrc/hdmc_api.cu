@@ -235,7 +235,7 @@ bool any_overlap(const hdmc_t* h, const HostState& hs) {
                             } else {
                                 const float ex = (float)qx + (float)dx * g.wxf, ey = (float)qy + (float)dy * g.wyf;
                                 const float ddx = (float)px - ex, ddy = (float)py - ey;
-                                if (std::fma(ddx, ddx, ddy * ddy) < g.sig2f) return true;
+                                if (std::fma(ddx, ddx, std::fma(ddy, ddy, -g.sig2f)) < 0.0f) return true;
                             }
                         }
                     }
@@ -244,11 +244,11 @@ bool any_overlap(const hdmc_t* h, const HostState& hs) {
     return false;
 }
 
-// Canonical host state <-> set-major device slots.
+// Canonical host state <-> set-major device cells (x0..x3 then y0..y3 per cell).
 void pack(const hdmc_t* h, const HostState& hs, std::vector<char>& raw) {
     const Geometry& g = h->g;
-    const size_t slot = h->prec == HDMC_FP64 ? sizeof(double2) : sizeof(float2);
-    raw.assign((size_t)g.C * kSlots * slot, 0);
+    const size_t el = h->prec == HDMC_FP64 ? sizeof(double) : sizeof(float);
+    raw.assign((size_t)g.C * 8 * el, 0);
     for (int cy = 0; cy < g.my; ++cy)
         for (int cx = 0; cx < g.mx; ++cx) {
             const int64_t c = (int64_t)cy * g.mx + cx;
@@ -257,11 +257,12 @@ void pack(const hdmc_t* h, const HostState& hs, std::vector<char>& raw) {
                 const double x = j < hs.cnt[c] ? hs.loc[2 * (4 * c + j)] : kEmpty;
                 const double y = j < hs.cnt[c] ? hs.loc[2 * (4 * c + j) + 1] : kEmpty;
                 if (h->prec == HDMC_FP64) {
-                    double2 v = make_double2(x, y);
-                    std::memcpy(raw.data() + (4 * s + j) * slot, &v, slot);
+                    std::memcpy(raw.data() + (8 * s + j) * el, &x, el);
+                    std::memcpy(raw.data() + (8 * s + 4 + j) * el, &y, el);
                 } else {
-                    float2 v = make_float2((float)x, (float)y);
-                    std::memcpy(raw.data() + (4 * s + j) * slot, &v, slot);
+                    const float fx = (float)x, fy = (float)y;
+                    std::memcpy(raw.data() + (8 * s + j) * el, &fx, el);
+                    std::memcpy(raw.data() + (8 * s + 4 + j) * el, &fy, el);
                 }
             }
         }
@@ -269,7 +270,7 @@ void pack(const hdmc_t* h, const HostState& hs, std::vector<char>& raw) {
 
 void unpack(const hdmc_t* h, const std::vector<char>& raw, HostState& hs) {
     const Geometry& g = h->g;
-    const size_t slot = h->prec == HDMC_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t el = h->prec == HDMC_FP64 ? sizeof(double) : sizeof(float);
     hs.loc.assign(8 * (size_t)g.C, kEmpty);
     hs.cnt.assign((size_t)g.C, 0);
     for (int cy = 0; cy < g.my; ++cy)
@@ -280,15 +281,14 @@ void unpack(const hdmc_t* h, const std::vector<char>& raw, HostState& hs) {
             for (int j = 0; j < kSlots; ++j) {
                 double x, y;
                 if (h->prec == HDMC_FP64) {
-                    double2 v;
-                    std::memcpy(&v, raw.data() + (4 * s + j) * slot, slot);
-                    x = v.x;
-                    y = v.y;
+                    std::memcpy(&x, raw.data() + (8 * s + j) * el, el);
+                    std::memcpy(&y, raw.data() + (8 * s + 4 + j) * el, el);
                 } else {
-                    float2 v;
-                    std::memcpy(&v, raw.data() + (4 * s + j) * slot, slot);
-                    x = v.x;
-                    y = v.y;
+                    float fx, fy;
+                    std::memcpy(&fx, raw.data() + (8 * s + j) * el, el);
+                    std::memcpy(&fy, raw.data() + (8 * s + 4 + j) * el, el);
+                    x = fx;
+                    y = fy;
                 }
                 if (x >= 0.0) n = j + 1;
                 hs.loc[2 * (4 * c + j)] = x >= 0.0 ? x : kEmpty;

@@ -1,123 +1,129 @@
-// hdmc_kernels.cuh -- sub-sweep, cell-shift and contact-histogram kernels,
-// templated on the coordinate type (double: HDMC_FP64, float:
-// HDMC_FP32_LOCAL).  Included once by each precision's translation unit.
+// hdmc_kernels.cuh -- sub-sweep, cell-shift and contact-histogram kernels.
+// Included once by each precision's translation unit.
+//
+// Cell storage (per cell, 4 slots): x0 x1 x2 x3 y0 y1 y2 y3 in the coordinate
+// type (32 B for binary32, 64 B for binary64); an unused slot holds kEmpty.
+// The cells of one checkerboard set are contiguous (see storage_index).
 //
 // Every floating-point operation that decides an acceptance, an ownership or
-// a histogram bin is written with an explicit round-to-nearest intrinsic, so
-// the result does not depend on compiler contraction: binary64 trial
-// positions are p + d*u (two roundings) and squared distances dx*dx + dy*dy
-// (three roundings); binary32 trial positions are fma(d, u, p) and squared
-// distances fma(dx, dx, dy*dy).
+// a histogram bin is written with an explicit round-to-nearest operation, so
+// the result does not depend on compiler contraction:
+//   binary64: trial coordinate p + d*u, overlap iff dx*dx + dy*dy < sigma^2;
+//   binary32: trial coordinate fma(d, u, p), overlap iff
+//             fma(dx, dx, fma(dy, dy, -sigma^2)) < 0.
 #pragma once
 
 #include "hdmc_device.cuh"
 
 namespace hdmc {
 
-template <typename T> struct Vec;
-template <> struct Vec<float> { using T2 = float2; };
-template <> struct Vec<double> { using T2 = double2; };
+constexpr int kDirChunk = 8;   // trial directions drawn ahead per thread (binary32 sub-sweep)
 
-// ---- arithmetic of one precision -------------------------------------------
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+// ---- packed binary32 pairs (Blackwell f32x2 arithmetic, IEEE round-to-nearest per lane) ----
+typedef unsigned long long f2x;
 
-// trial coordinate p + d*u
-__device__ __forceinline__ float trial_coord(float d, float u, float p) { return __fmaf_rn(d, u, p); }
-__device__ __forceinline__ double trial_coord(double d, double u, double p) { return __dadd_rn(p, __dmul_rn(d, u)); }
-
-// squared distance compared with sigma^2: overlap iff r^2 < sigma^2
-__device__ __forceinline__ bool overlaps(float dx, float dy, float s2) {
-    return __fmaf_rn(dx, dx, __fmul_rn(dy, dy)) < s2;
+__device__ __forceinline__ f2x pk(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
-__device__ __forceinline__ bool overlaps(double dx, double dy, double s2) {
-    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < s2;
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint32_t lo32(f2x v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t hi32(f2x v) { return (uint32_t)(v >> 32); }
+
+// z = fma(dx, dx, fma(dy, dy, -sigma^2)) for two candidates at once; the sign
+// bit of each half is set iff that candidate overlaps the trial position.
+__device__ __forceinline__ f2x zpair(f2x tx2, f2x ty2, f2x qx2, f2x qy2, f2x ns2) {
+    const f2x dx = sub2(tx2, qx2);
+    const f2x dy = sub2(ty2, qy2);
+    return fma2(dx, dx, fma2(dy, dy, ns2));
 }
 
-template <typename T> struct Prm;
-template <> struct Prm<float> {
-    static __device__ __forceinline__ float wx(const Geometry& g) { return g.wxf; }
-    static __device__ __forceinline__ float wy(const Geometry& g) { return g.wyf; }
-    static __device__ __forceinline__ float d(const Geometry& g) { return g.df; }
-    static __device__ __forceinline__ float s2(const Geometry& g) { return g.sig2f; }
-    static __device__ __forceinline__ float ds(const SweepDraw& r) { return r.dsf; }
-    static __device__ __forceinline__ float prev(float w) { return __uint_as_float(__float_as_uint(w) - 1u); }
-    // Direction of a trial move, uniform in the unit disk: two 23-bit
-    // symmetric variates per attempt, two attempts per Philox block.
-    static __device__ __forceinline__ void direction(const Geometry& g, uint32_t s0, uint32_t s1, uint32_t s2,
-                                                     float& u, float& v) {
-        uint4 c = make_uint4(s0, s1, s2, 0u);
-        for (;;) {
-            const uint4 r = philox4x32_10(c, g.key0, g.key1);
-            u = sym23(r.x);
-            v = sym23(r.y);
-            if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) return;
-            u = sym23(r.z);
-            v = sym23(r.w);
-            if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) return;
-            c.w += 1u;
-        }
-    }
-};
-template <> struct Prm<double> {
-    static __device__ __forceinline__ double wx(const Geometry& g) { return g.wx; }
-    static __device__ __forceinline__ double wy(const Geometry& g) { return g.wy; }
-    static __device__ __forceinline__ double d(const Geometry& g) { return g.d; }
-    static __device__ __forceinline__ double s2(const Geometry& g) { return g.sig2; }
-    static __device__ __forceinline__ double ds(const SweepDraw& r) { return r.ds; }
-    static __device__ __forceinline__ double prev(double w) {
-        return __longlong_as_double(__double_as_longlong(w) - 1ll);
-    }
-    // Two 52-bit symmetric variates per attempt, one Philox block each.
-    static __device__ __forceinline__ void direction(const Geometry& g, uint32_t s0, uint32_t s1, uint32_t s2,
-                                                     double& u, double& v) {
-        uint4 c = make_uint4(s0, s1, s2, 0u);
-        for (;;) {
-            const uint4 r = philox4x32_10(c, g.key0, g.key1);
-            u = sym52(r.x, r.y);
-            v = sym52(r.z, r.w);
-            if (__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) < 1.0) return;
-            c.w += 1u;
-        }
-    }
-};
+// ---- 21-bit fields of a Philox block (binary32 draws) -------------------------
+// Field j = bits [21j, 21j+21) of the 128-bit integer w.x + 2^32 w.y + 2^64 w.z + 2^96 w.w.
+__device__ __forceinline__ void fields21(const uint4 w, uint32_t f[6]) {
+    const uint32_t M = 0x1FFFFFu;
+    f[0] = w.x & M;
+    f[1] = __funnelshift_r(w.x, w.y, 21) & M;
+    f[2] = (w.y >> 10) & M;
+    f[3] = __funnelshift_r(w.y, w.z, 31) & M;
+    f[4] = __funnelshift_r(w.z, w.w, 20) & M;
+    f[5] = (w.w >> 9) & M;
+}
+// Odd multiples of 2^-21 in (-1,1).
+__device__ __forceinline__ float sym21(uint32_t f) {
+    return (float)((int32_t)(2 * f + 1) - (1 << 21)) * 0x1p-21f;
+}
 
-// ---- cell loads / stores -----------------------------------------------------
-__device__ __forceinline__ void load_cell(const float2* p, float x[4], float y[4]) {
+// Uniform permutation of n <= 4 slots from k in [0, n!): Fisher-Yates swaps
+// j <-> k mod (j+1), k /= (j+1), for j = n-1 down to 1.  Returned packed: byte
+// j = old slot that moves to slot j.
+__device__ __forceinline__ uint32_t perm_from_index(int n, uint32_t k) {
+    uint32_t pk = 0x03020100u;
+    auto swap = [&](int a, int b) {
+        const uint32_t va = (pk >> (8 * a)) & 0xFFu, vb = (pk >> (8 * b)) & 0xFFu;
+        pk &= ~((0xFFu << (8 * a)) | (0xFFu << (8 * b)));
+        pk |= (va << (8 * b)) | (vb << (8 * a));
+    };
+    if (n >= 4) { swap(3, (int)(k & 3u)); k >>= 2; }
+    if (n >= 3) { swap(2, (int)(k % 3u)); k /= 3u; }
+    if (n >= 2) { swap(1, (int)(k & 1u)); }
+    return pk;
+}
+
+__device__ __forceinline__ uint32_t factorial(int n) { return n == 4 ? 24u : n == 3 ? 6u : n == 2 ? 2u : 1u; }
+
+// ---- cells ---------------------------------------------------------------------
+template <typename T> struct Cell { T x[4], y[4]; };
+
+__device__ __forceinline__ void load_cell(const float* p, Cell<float>& c) {
     const float4 a = reinterpret_cast<const float4*>(p)[0];
     const float4 b = reinterpret_cast<const float4*>(p)[1];
-    x[0] = a.x; y[0] = a.y; x[1] = a.z; y[1] = a.w;
-    x[2] = b.x; y[2] = b.y; x[3] = b.z; y[3] = b.w;
+    c.x[0] = a.x; c.x[1] = a.y; c.x[2] = a.z; c.x[3] = a.w;
+    c.y[0] = b.x; c.y[1] = b.y; c.y[2] = b.z; c.y[3] = b.w;
 }
-__device__ __forceinline__ void load_cell_ro(const float2* p, float x[4], float y[4]) {
+__device__ __forceinline__ void load_cell_ro(const float* p, Cell<float>& c) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(p));
     const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-    x[0] = a.x; y[0] = a.y; x[1] = a.z; y[1] = a.w;
-    x[2] = b.x; y[2] = b.y; x[3] = b.z; y[3] = b.w;
+    c.x[0] = a.x; c.x[1] = a.y; c.x[2] = a.z; c.x[3] = a.w;
+    c.y[0] = b.x; c.y[1] = b.y; c.y[2] = b.z; c.y[3] = b.w;
 }
-__device__ __forceinline__ void store_cell(float2* p, const float x[4], const float y[4]) {
-    reinterpret_cast<float4*>(p)[0] = make_float4(x[0], y[0], x[1], y[1]);
-    reinterpret_cast<float4*>(p)[1] = make_float4(x[2], y[2], x[3], y[3]);
+__device__ __forceinline__ void store_cell(float* p, const Cell<float>& c) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(c.x[0], c.x[1], c.x[2], c.x[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(c.y[0], c.y[1], c.y[2], c.y[3]);
 }
-__device__ __forceinline__ void load_cell(const double2* p, double x[4], double y[4]) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const double2 a = p[j];
-        x[j] = a.x; y[j] = a.y;
-    }
+__device__ __forceinline__ void load_cell(const double* p, Cell<double>& c) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = q[0], b = q[1], e = q[2], f = q[3];
+    c.x[0] = a.x; c.x[1] = a.y; c.x[2] = b.x; c.x[3] = b.y;
+    c.y[0] = e.x; c.y[1] = e.y; c.y[2] = f.x; c.y[3] = f.y;
 }
-__device__ __forceinline__ void load_cell_ro(const double2* p, double x[4], double y[4]) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const double2 a = __ldg(p + j);
-        x[j] = a.x; y[j] = a.y;
-    }
+__device__ __forceinline__ void load_cell_ro(const double* p, Cell<double>& c) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldg(q), b = __ldg(q + 1), e = __ldg(q + 2), f = __ldg(q + 3);
+    c.x[0] = a.x; c.x[1] = a.y; c.x[2] = b.x; c.x[3] = b.y;
+    c.y[0] = e.x; c.y[1] = e.y; c.y[2] = f.x; c.y[3] = f.y;
 }
-__device__ __forceinline__ void store_cell(double2* p, const double x[4], const double y[4]) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) p[j] = make_double2(x[j], y[j]);
+__device__ __forceinline__ void store_cell(double* p, const Cell<double>& c) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(c.x[0], c.x[1]);
+    q[1] = make_double2(c.x[2], c.x[3]);
+    q[2] = make_double2(c.y[0], c.y[1]);
+    q[3] = make_double2(c.y[2], c.y[3]);
 }
 
 template <typename T>
@@ -125,111 +131,35 @@ __device__ __forceinline__ T pick(const T a[4], int i) {
     return i == 0 ? a[0] : i == 1 ? a[1] : i == 2 ? a[2] : a[3];
 }
 template <typename T>
-__device__ __forceinline__ void put(T a[4], int i, T v) {
+__device__ __forceinline__ void put_if(T a[4], int i, T v, bool p) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = (i == j) ? v : a[j];
+    for (int j = 0; j < 4; ++j) a[j] = (p && i == j) ? v : a[j];
+}
+template <typename T>
+__device__ __forceinline__ void permute(T a[4], uint32_t pk) {
+    T r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[j] = pick(a, (int)((pk >> (8 * j)) & 0xFFu));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = r[j];
 }
 
 __device__ __forceinline__ int wrap(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
 
-// ---- sub-sweep: Alg. 1 lines 4-13 / Alg. 2 -----------------------------------
-// One thread per active cell of set Q = draw->perm[k]; block 32 x 4 over the
-// set's half-resolution grid.  Each thread shuffles its cell, then makes n_M
-// trial moves, visiting the shuffled slots cyclically.  A trial is rejected if
-// it leaves [0,wx) x [0,wy), else if it overlaps another disk of the cell or a
-// disk of the 8 neighbouring cells (translated by their cell offset).  The
-// neighbours belong to other sets and are not written by this launch.
-template <typename T>
-__global__ void __launch_bounds__(128)
-k_subsweep(const Geometry g, typename Vec<T>::T2* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
-           unsigned long long* __restrict__ partial) {
-    using T2 = typename Vec<T>::T2;
-    const int Q = draw->perm[k];
-    const uint32_t sweep = draw->sweep;
-    const int qx = Q & 1, qy = Q >> 1;
-    const int hx = blockIdx.x * 32 + threadIdx.x;
-    const int hy = blockIdx.y * 4 + threadIdx.y;
-    unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
-    if (hx < g.hx && hy < g.hy) {
-        const int cx = 2 * hx + qx, cy = 2 * hy + qy;
-        T2* own = cells + 4 * ((long long)Q * g.cq + (long long)hy * g.hx + hx);
-        T x[4], y[4];
-        load_cell(own, x, y);
-        const int n = (x[0] >= T(0)) + (x[1] >= T(0)) + (x[2] >= T(0)) + (x[3] >= T(0));
-        if (n > 0) {
-            const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
-            const uint32_t setbits = (uint32_t)Q << 24;
-            // Fisher-Yates shuffle of the occupied slots (Alg. 1 line 5)
-            if (n >= 2) {
-                WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
-                uint32_t pk = 0x03020100u;   // byte j = old slot now at j
-                for (int j = n - 1; j >= 1; --j) {
-                    const int kk = (int)s.bounded((uint32_t)(j + 1));
-                    const uint32_t aj = (pk >> (8 * j)) & 0xFFu, ak = (pk >> (8 * kk)) & 0xFFu;
-                    pk &= ~((0xFFu << (8 * j)) | (0xFFu << (8 * kk)));
-                    pk |= (aj << (8 * kk)) | (ak << (8 * j));
-                }
-                T nx[4], ny[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int src = (pk >> (8 * j)) & 0xFF;
-                    nx[j] = pick(x, src);
-                    ny[j] = pick(y, src);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { x[j] = nx[j]; y[j] = ny[j]; }
-            }
-            // the 8 neighbouring cells, translated into this cell's frame
-            T qxs[32], qys[32];
-            const T wxs = Prm<T>::wx(g), wys = Prm<T>::wy(g);
-            int m = 0;
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (dx == 0 && dy == 0) continue;
-                    const int ncx = wrap(cx + dx, g.mx), ncy = wrap(cy + dy, g.my);
-                    T ax[4], ay[4];
-                    load_cell_ro(cells + 4 * storage_index(g, ncx, ncy), ax, ay);
-                    const T sx = T(dx) * wxs, sy = T(dy) * wys;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        qxs[m + j] = add_rn(ax[j], sx);
-                        qys[m + j] = add_rn(ay[j], sy);
-                    }
-                    m += 4;
-                }
-            }
-            const T d = Prm<T>::d(g), s2 = Prm<T>::s2(g);
-            int i = 0;
-            for (int t = 0; t < g.nsel; ++t) {
-                T u, v;
-                Prm<T>::direction(g, sweep, cell, (kDomTrial << 28) | setbits | (uint32_t)t, u, v);
-                const T px = pick(x, i), py = pick(y, i);
-                const T tx = trial_coord(d, u, px), ty = trial_coord(d, v, py);
-                ++n_tr;
-                if (tx >= T(0) && tx < wxs && ty >= T(0) && ty < wys) {
-                    bool hit = false;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        hit |= (j != i) && overlaps(sub_rn(tx, x[j]), sub_rn(ty, y[j]), s2);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        hit |= overlaps(sub_rn(tx, qxs[j]), sub_rn(ty, qys[j]), s2);
-                    if (!hit) {
-                        put(x, i, tx);
-                        put(y, i, ty);
-                        ++n_acc;
-                    }
-                } else {
-                    ++n_leave;
-                }
-                i = (i + 1 == n) ? 0 : i + 1;
-            }
-            store_cell(own, x, y);
-        }
-    }
-    // per-block counters: partial[4b + {trials, accepted, left, overlap}]
+// Truncating binary64 -> binary32 with integer instructions only (relative
+// error < 2^-23; magnitudes below 2^-126 become 0).  Used for conservative
+// prefilters, never for a decision.
+__device__ __forceinline__ float approx_f32(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return e < 897u ? __uint_as_float(hi & 0x80000000u) : __uint_as_float(f);
+}
+
+// per-block trial counters: partial[4b + {trials, accepted, left, overlap}]
+__device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned int n_acc, unsigned int n_leave,
+                                                   unsigned long long* __restrict__ partial) {
     __shared__ unsigned int red[4][3];
     const unsigned a = __reduce_add_sync(0xffffffffu, n_tr);
     const unsigned b = __reduce_add_sync(0xffffffffu, n_acc);
@@ -252,50 +182,329 @@ k_subsweep(const Geometry g, typename Vec<T>::T2* __restrict__ cells, const Swee
     }
 }
 
-// ---- cell shift: Alg. 4 ---------------------------------------------------------
-// One thread per new cell (storage order).  New cell c = the disks of old c
-// that stay inside c after the translation by -f*ds (old slot order), then
-// the disks of old c+f that leave c+f, re-expressed in c's frame (+f*w).  The
-// ownership test is the same expression in the two threads that see a disk,
-// so every disk lands in exactly one cell (Sec. 3.2).  A re-expressed value
-// that rounds onto the upper edge is clamped to the largest value below it.
+// ---- neighbourhood of an active cell on the set-major layout ---------------------------
+// For a cell of set Q = qx + 2 qy at half-grid position (hx, hy), the
+// neighbours (cx +- 1, cy) lie in set Q^1 at half-columns xl, xr, the
+// neighbours (cx, cy +- 1) in set Q^2 at half-rows yd, yu, the diagonal ones
+// in set Q^3 (periodic wrap on the half grid).  Directions c = 0..7 run over
+// (dx,dy) = (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1).
+struct Neighbourhood {
+    long long base[4];   // first cell of set Q, Q^1, Q^2, Q^3
+    int xl, xr, yd, yu;
+    __device__ Neighbourhood(const Geometry& g, int Q, int hx, int hy) {
+        const int qx = Q & 1, qy = Q >> 1;
+        base[0] = (long long)Q * g.cq;
+        base[1] = (long long)(Q ^ 1) * g.cq;
+        base[2] = (long long)(Q ^ 2) * g.cq;
+        base[3] = (long long)(Q ^ 3) * g.cq;
+        xl = hx - 1 + qx;
+        xl = xl < 0 ? g.hx - 1 : xl;
+        xr = hx + qx;
+        xr = xr >= g.hx ? 0 : xr;
+        yd = hy - 1 + qy;
+        yd = yd < 0 ? g.hy - 1 : yd;
+        yu = hy + qy;
+        yu = yu >= g.hy ? 0 : yu;
+    }
+    __device__ __forceinline__ long long index(const Geometry& g, int c, int hx, int hy) const {
+        const int col = (c == 1 || c == 6) ? hx : ((c == 0 || c == 3 || c == 5) ? xl : xr);
+        const int row = (c < 3) ? yd : (c < 5 ? hy : yu);
+        const int set = (c == 3 || c == 4) ? 1 : ((c == 1 || c == 6) ? 2 : 3);
+        return base[set] + (long long)row * g.hx + col;
+    }
+};
+__device__ __forceinline__ int dir_dx(int c) { return (c == 1 || c == 6) ? 0 : ((c == 0 || c == 3 || c == 5) ? -1 : 1); }
+__device__ __forceinline__ int dir_dy(int c) { return c < 3 ? -1 : (c < 5 ? 0 : 1); }
+
+// ---- binary32 sub-sweep: Alg. 1 lines 4-13 / Alg. 2 ----------------------------------
+// One thread per active cell of set Q = draw->perm[k]; block 32 x 4 over the
+// set's half-resolution grid.  The thread draws its cell's shuffle and trial
+// directions from the cell's stream (kept directions staged in shared
+// memory), shuffles its disks, then makes n_M trial moves visiting the slots
+// cyclically.  The 8 neighbouring cells belong to other sets and are not
+// written by this launch.  Their slot pair (0,1), translated into this
+// cell's frame, is held in registers as packed binary32 pairs; their slot
+// pair (2,3) is read (from L1) and tested only in directions where some lane
+// of the warp has a third disk.
+static __global__ void __launch_bounds__(128, 5)
+k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
+               unsigned long long* __restrict__ partial) {
+    __shared__ float2 sdir[kDirChunk][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int Q = draw->perm[k];
+    const uint32_t sweep = draw->sweep;
+    const int hx = blockIdx.x * 32 + threadIdx.x;
+    const int hy = blockIdx.y * 4 + threadIdx.y;
+    const bool live = hx < g.hx && hy < g.hy;
+    const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
+    const Neighbourhood nbh(g, Q, hx, hy);
+
+    Cell<float> own;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = (float)kEmpty;
+    float* ownp = cells + 8 * (nbh.base[0] + (long long)hy * g.hx + hx);
+    if (live) load_cell(ownp, own);
+    // slots 0,1 of the neighbours; slot 2 only to know whether it is used
+    float4 n01[8];
+    float n2[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        n01[c] = make_float4((float)kEmpty, (float)kEmpty, (float)kEmpty, (float)kEmpty);
+        n2[c] = (float)kEmpty;
+        if (live) {
+            const float* p = cells + 8 * nbh.index(g, c, hx, hy);
+            const float2 x01 = __ldg(reinterpret_cast<const float2*>(p));
+            const float2 y01 = __ldg(reinterpret_cast<const float2*>(p) + 2);
+            n01[c] = make_float4(x01.x, x01.y, y01.x, y01.y);
+            n2[c] = __ldg(p + 2);
+        }
+    }
+    const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
+    uint32_t dir23 = 0;   // warp-uniform: directions where some lane has a third disk
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dir23 |= __any_sync(0xffffffffu, n2[c] >= 0.f) ? (1u << c) : 0u;
+    const bool own23 = __any_sync(0xffffffffu, n >= 3);
+
+    unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
+    if (n > 0) {
+        const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+        const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
+        uint32_t blk = 0;
+        uint32_t F[6];
+        fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
+        // shuffle (Alg. 1 line 5): one draw in [0, n!) by 21-bit Lemire on field 0
+        if (n >= 2) {
+            const uint32_t range = factorial(n);
+            const uint32_t m = F[0] * range;
+            const uint32_t thr = n == 4 ? 8u : (n == 3 ? 2u : 0u);   // 2^21 mod n!
+            uint32_t kk = m >> 21;
+            if ((m & 0x1FFFFFu) < thr) {   // rejected: draw from the shuffle stream instead
+                WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | ((uint32_t)Q << 24));
+                kk = s.bounded(range);
+            }
+            const uint32_t pk = perm_from_index(n, kk);
+            permute(own.x, pk);
+            permute(own.y, pk);
+        }
+        // neighbour slots 0,1 translated into this cell's frame
+        f2x qx01[8], qy01[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
+            qx01[c] = add2(pk(n01[c].x, n01[c].y), pk(sx, sx));
+            qy01[c] = add2(pk(n01[c].z, n01[c].w), pk(sy, sy));
+        }
+        const float df = g.df;
+        const f2x ns2 = pk(-g.sig2f, -g.sig2f);
+        int pnext = 1;   // next attempt: field pair 1 of block 0 (fields 2,3)
+        int i = 0;
+        for (int t0 = 0; t0 < g.nsel; t0 += kDirChunk) {
+            const int want = min(kDirChunk, g.nsel - t0);
+            // directions: attempts (u,v) from consecutive field pairs, kept inside the unit disk
+            int have = 0;
+            for (;;) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    if (p >= pnext && have < want) {
+                        const float u = sym21(F[2 * p]), v = sym21(F[2 * p + 1]);
+                        if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) {
+                            sdir[have][tid] = make_float2(u, v);
+                            ++have;
+                        }
+                        pnext = p + 1;
+                    }
+                }
+                if (have >= want) break;
+                ++blk;
+                fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+                pnext = 0;
+            }
+            for (int tt = 0; tt < want; ++tt) {
+                const float2 uv = sdir[tt][tid];
+                const float tx = __fmaf_rn(df, uv.x, pick(own.x, i));
+                const float ty = __fmaf_rn(df, uv.y, pick(own.y, i));
+                const bool inside = tx >= 0.f && tx < g.wxf && ty >= 0.f && ty < g.wyf;
+                const f2x tx2 = pk(tx, tx), ty2 = pk(ty, ty);
+                // own cell: every other occupied slot (slot i excluded)
+                f2x z = zpair(tx2, ty2, pk(own.x[0], own.x[1]), pk(own.y[0], own.y[1]), ns2);
+                uint32_t acc = (i == 0 ? 0u : lo32(z)) | (i == 1 ? 0u : hi32(z));
+                if (own23) {
+                    z = zpair(tx2, ty2, pk(own.x[2], own.x[3]), pk(own.y[2], own.y[3]), ns2);
+                    acc |= (i == 2 ? 0u : lo32(z)) | (i == 3 ? 0u : hi32(z));
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    z = zpair(tx2, ty2, qx01[c], qy01[c], ns2);
+                    acc |= lo32(z) | hi32(z);
+                }
+                for (uint32_t m = dir23; m; m &= m - 1) {   // warp-uniform, rarely taken
+                    const int c = __ffs(m) - 1;
+                    const float2* p = reinterpret_cast<const float2*>(cells + 8 * nbh.index(g, c, hx, hy));
+                    const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
+                    const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
+                    z = zpair(tx2, ty2, add2(pk(x23.x, x23.y), pk(sx, sx)), add2(pk(y23.x, y23.y), pk(sy, sy)), ns2);
+                    acc |= lo32(z) | hi32(z);
+                }
+                const bool ok = inside && !(acc & 0x80000000u);
+                put_if(own.x, i, tx, ok);
+                put_if(own.y, i, ty, ok);
+                n_acc += ok;
+                n_leave += !inside;
+                i = (i + 1 == n) ? 0 : i + 1;
+            }
+        }
+        n_tr = (unsigned)g.nsel;
+        store_cell(ownp, own);
+    }
+    add_block_counters(n_tr, n_acc, n_leave, partial);
+}
+
+// ---- binary64 sub-sweep ---------------------------------------------------------------
+// Same algorithm in binary64.  Draws: shuffle by one 32-bit Lemire draw in
+// [0, n!) from the cell's shuffle stream; trial t takes the t-th kept attempt
+// of the trial stream, attempt a = block a.
+static __global__ void __launch_bounds__(128)
+k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
+               unsigned long long* __restrict__ partial) {
+    const int Q = draw->perm[k];
+    const uint32_t sweep = draw->sweep;
+    const int qx = Q & 1, qy = Q >> 1;
+    const int hx = blockIdx.x * 32 + threadIdx.x;
+    const int hy = blockIdx.y * 4 + threadIdx.y;
+    unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
+    if (hx < g.hx && hy < g.hy) {
+        const int cx = 2 * hx + qx, cy = 2 * hy + qy;
+        double* ownp = cells + 8 * ((long long)Q * g.cq + (long long)hy * g.hx + hx);
+        Cell<double> own;
+        load_cell(ownp, own);
+        const int n = (own.x[0] >= 0.0) + (own.x[1] >= 0.0) + (own.x[2] >= 0.0) + (own.x[3] >= 0.0);
+        if (n > 0) {
+            const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+            const uint32_t setbits = (uint32_t)Q << 24;
+            if (n >= 2) {
+                WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
+                const uint32_t pk = perm_from_index(n, s.bounded(factorial(n)));
+                permute(own.x, pk);
+                permute(own.y, pk);
+            }
+            double qxs[32], qys[32];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int dx = (c < 3) ? c - 1 : (c == 3 ? -1 : (c == 4 ? 1 : c - 6));
+                const int dy = (c < 3) ? -1 : (c < 5 ? 0 : 1);
+                Cell<double> a;
+                load_cell_ro(cells + 8 * storage_index(g, wrap(cx + dx, g.mx), wrap(cy + dy, g.my)), a);
+                const double sx = (double)dx * g.wx, sy = (double)dy * g.wy;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    qxs[4 * c + j] = __dadd_rn(a.x[j], sx);
+                    qys[4 * c + j] = __dadd_rn(a.y[j], sy);
+                }
+            }
+            uint32_t blk = 0;
+            const uint32_t c2 = (kDomTrial << 28) | setbits;
+            int i = 0;
+            for (int t = 0; t < g.nsel; ++t) {
+                double u, v;
+                for (;;) {
+                    const uint4 r = philox4x32_10(make_uint4(sweep, cell, c2, blk++), g.key0, g.key1);
+                    u = sym52(r.x, r.y);
+                    v = sym52(r.z, r.w);
+                    if (__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) < 1.0) break;
+                }
+                const double tx = __dadd_rn(pick(own.x, i), __dmul_rn(g.d, u));
+                const double ty = __dadd_rn(pick(own.y, i), __dmul_rn(g.d, v));
+                ++n_tr;
+                if (tx >= 0.0 && tx < g.wx && ty >= 0.0 && ty < g.wy) {
+                    bool hit = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const double ddx = __dsub_rn(tx, own.x[j]), ddy = __dsub_rn(ty, own.y[j]);
+                        hit |= (j != i) && (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const double ddx = __dsub_rn(tx, qxs[j]), ddy = __dsub_rn(ty, qys[j]);
+                        hit |= __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2;
+                    }
+                    if (!hit) {
+                        put_if(own.x, i, tx, true);
+                        put_if(own.y, i, ty, true);
+                        ++n_acc;
+                    }
+                } else {
+                    ++n_leave;
+                }
+                i = (i + 1 == n) ? 0 : i + 1;
+            }
+            store_cell(ownp, own);
+        }
+    }
+    add_block_counters(n_tr, n_acc, n_leave, partial);
+}
+
+// ---- cell shift: Alg. 4 ----------------------------------------------------------------
+// One thread per new cell; grid (set row, set column, set).  New cell c = the
+// disks of old c that stay inside c after the translation by -f*ds (old slot
+// order), then the disks of old c+f that leave c+f, re-expressed in c's frame
+// (+f*w).  The ownership test is the same expression in the two threads that
+// see a disk, so every disk lands in exactly one cell (Sec. 3.2).  A
+// re-expressed value that rounds onto the upper edge is clamped below it.
+template <typename T> struct Prm;
+template <> struct Prm<float> {
+    static __device__ __forceinline__ float wx(const Geometry& g) { return g.wxf; }
+    static __device__ __forceinline__ float wy(const Geometry& g) { return g.wyf; }
+    static __device__ __forceinline__ float ds(const SweepDraw& r) { return r.dsf; }
+    static __device__ __forceinline__ float prev(float w) { return __uint_as_float(__float_as_uint(w) - 1u); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+};
+template <> struct Prm<double> {
+    static __device__ __forceinline__ double wx(const Geometry& g) { return g.wx; }
+    static __device__ __forceinline__ double wy(const Geometry& g) { return g.wy; }
+    static __device__ __forceinline__ double ds(const SweepDraw& r) { return r.ds; }
+    static __device__ __forceinline__ double prev(double w) {
+        return __longlong_as_double(__double_as_longlong(w) - 1ll);
+    }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_shift(const Geometry g, const typename Vec<T>::T2* __restrict__ src, typename Vec<T>::T2* __restrict__ dst,
-        const SweepDraw* __restrict__ draw, DevState* __restrict__ st) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const SweepDraw* __restrict__ draw,
+        DevState* __restrict__ st) {
+    const int hx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int hy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int q = blockIdx.z;
     const int fdir = draw->fdir;
     const int ax = fdir >> 1;
     const int sgn = (fdir & 1) ? -1 : 1;
     const T w = ax ? Prm<T>::wy(g) : Prm<T>::wx(g);
     const T sd = T(sgn) * Prm<T>::ds(*draw);
     const T sw = T(sgn) * w;
-    if (idx == 0) st->origin[ax] += (double)sd;
-    if (idx >= g.C) return;
-    const int q = (int)(idx / g.cq);
-    const long long r = idx - (long long)q * g.cq;
-    const int hy = (int)(r / g.hx);
-    const int hx = (int)(r - (long long)hy * g.hx);
+    if (hx == 0 && hy == 0 && q == 0) st->origin[ax] += (double)sd;
+    if (hx >= g.hx || hy >= g.hy) return;
     const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
     const int ncx = ax ? cx : wrap(cx + sgn, g.mx);
     const int ncy = ax ? wrap(cy + sgn, g.my) : cy;
-    T ox[4], oy[4], bx[4], by[4];
-    load_cell_ro(src + 4 * idx, ox, oy);
-    load_cell_ro(src + 4 * storage_index(g, ncx, ncy), bx, by);
-    T rx[4], ry[4];
+    const long long idx = (long long)q * g.cq + (long long)hy * g.hx + hx;
+    Cell<T> o, b, r;
+    load_cell_ro(src + 8 * idx, o);
+    load_cell_ro(src + 8 * storage_index(g, ncx, ncy), b);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { rx[j] = T(kEmpty); ry[j] = T(kEmpty); }
+    for (int j = 0; j < 4; ++j) r.x[j] = r.y[j] = T(kEmpty);
     int kept = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (ox[j] >= T(0)) {
-            const T dp = sub_rn(ax ? oy[j] : ox[j], sd);
+        if (o.x[j] >= T(0)) {
+            const T dp = Prm<T>::sub(ax ? o.y[j] : o.x[j], sd);
             if (dp >= T(0) && dp < w) {
-                const T vx = ax ? ox[j] : dp, vy = ax ? dp : oy[j];
+                const T vx = ax ? o.x[j] : dp, vy = ax ? dp : o.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    rx[s] = (kept == s) ? vx : rx[s];
-                    ry[s] = (kept == s) ? vy : ry[s];
+                    r.x[s] = (kept == s) ? vx : r.x[s];
+                    r.y[s] = (kept == s) ? vy : r.y[s];
                 }
                 ++kept;
             }
@@ -303,98 +512,133 @@ k_shift(const Geometry g, const typename Vec<T>::T2* __restrict__ src, typename 
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (bx[j] >= T(0)) {
-            const T dp = sub_rn(ax ? by[j] : bx[j], sd);
+        if (b.x[j] >= T(0)) {
+            const T dp = Prm<T>::sub(ax ? b.y[j] : b.x[j], sd);
             if (!(dp >= T(0) && dp < w)) {
-                T v = add_rn(dp, sw);
+                T v = Prm<T>::add(dp, sw);
                 v = (v >= w) ? Prm<T>::prev(w) : v;
                 v = (v < T(0)) ? T(0) : v;
-                const T vx = ax ? bx[j] : v, vy = ax ? v : by[j];
+                const T vx = ax ? b.x[j] : v, vy = ax ? v : b.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    rx[s] = (kept == s) ? vx : rx[s];
-                    ry[s] = (kept == s) ? vy : ry[s];
+                    r.x[s] = (kept == s) ? vx : r.x[s];
+                    r.y[s] = (kept == s) ? vy : r.y[s];
                 }
                 ++kept;
             }
         }
     }
     if (kept > 4) atomicOr(&st->error, 1u);
-    store_cell(dst + 4 * idx, rx, ry);
+    store_cell(dst + 8 * idx, r);
 }
 
 // ---- contact histogram: Sec. 4 ------------------------------------------------------
 // Ordered pairs (i, j != i) at distance r in [sigma, sigma + 200 dr), bin
-// floor((r - sigma)/dr), distances in binary64 from cell-local coordinates
-// over the 5x5 neighbourhood (w >= sigma, so two rings reach past 1.02 sigma).
-// Grid-stride over cells; per-block shared histogram, one atomic per bin.
+// floor((r - sigma)/dr), the distance taken in binary64 from cell-local
+// coordinates over the 5x5 neighbourhood (w >= sigma, so two rings reach past
+// 1.02 sigma).  A binary32 estimate of r^2 with a wide margin selects the
+// candidates; only those get the binary64 distance.  One thread per cell,
+// grid (set row, set column, set); per-block shared histogram.
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return approx_f32(v); }
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_hist(const Geometry g, const typename Vec<T>::T2* __restrict__ cells, unsigned long long* __restrict__ hist) {
+k_hist(const Geometry g, const T* __restrict__ cells, unsigned long long* __restrict__ hist) {
     __shared__ unsigned int sh[kHistBins];
-    for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) sh[b] = 0u;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y) sh[b] = 0u;
     __syncthreads();
-    const double wxd = (double)Prm<T>::wx(g), wyd = (double)Prm<T>::wy(g);
-    const double sigma = g.sigma, dr = kHistDr * g.sigma;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.C;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(idx / g.cq);
-        const long long r = idx - (long long)q * g.cq;
-        const int hy = (int)(r / g.hx);
-        const int hx = (int)(r - (long long)hy * g.hx);
-        const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
-        T px[4], py[4];
-        load_cell_ro(cells + 4 * idx, px, py);
-        if (!(px[0] >= T(0))) continue;
+    const int hx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int hy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int q = blockIdx.z;
+    const bool live = hx < g.hx && hy < g.hy;
+    Cell<T> own;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = T(kEmpty);
+    const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
+    if (live) load_cell_ro(cells + 8 * ((long long)q * g.cq + (long long)hy * g.hx + hx), own);
+    const bool any = __any_sync(0xffffffffu, own.x[0] >= T(0));
+    const bool own23 = __any_sync(0xffffffffu, own.x[2] >= T(0));
+    if (any) {
+        const double wxd = (double)Prm<T>::wx(g), wyd = (double)Prm<T>::wy(g);
+        const float wxf = (float)Prm<T>::wx(g), wyf = (float)Prm<T>::wy(g);
+        const double sigma = g.sigma, dr = kHistDr * g.sigma;
+        const float rmax = (float)(g.sigma + kHistBins * dr);
+        const float thr = rmax * rmax * 1.001f;   // binary32 estimate margin (estimate error < 1e-6)
+        float ox[4], oy[4];
+        uint32_t occupied = 0;   // bits 4i..4i+3 set when own slot i holds a disk
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ox[i] = to_f32(own.x[i]);
+            oy[i] = to_f32(own.y[i]);
+            occupied |= own.x[i] >= T(0) ? (0xFu << (4 * i)) : 0u;
+        }
         for (int dy = -2; dy <= 2; ++dy) {
             for (int dx = -2; dx <= 2; ++dx) {
-                const int ncx = wrap(cx + dx, g.mx), ncy = wrap(cy + dy, g.my);
-                T qx[4], qy[4];
-                load_cell_ro(cells + 4 * storage_index(g, ncx, ncy), qx, qy);
-                const double sx = (double)dx * wxd, sy = (double)dy * wyd;
+                Cell<T> c;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!(qx[j] >= T(0))) continue;
-                    const double ex = __dadd_rn((double)qx[j], sx), ey = __dadd_rn((double)qy[j], sy);
+                for (int j = 0; j < 4; ++j) c.x[j] = c.y[j] = T(kEmpty);
+                if (live) load_cell_ro(cells + 8 * storage_index(g, wrap(cx + dx, g.mx), wrap(cy + dy, g.my)), c);
+                const float sxf = (float)dx * wxf, syf = (float)dy * wyf;
+                const f2x qx01 = add2(pk(to_f32(c.x[0]), to_f32(c.x[1])), pk(sxf, sxf));
+                const f2x qx23 = add2(pk(to_f32(c.x[2]), to_f32(c.x[3])), pk(sxf, sxf));
+                const f2x qy01 = add2(pk(to_f32(c.y[0]), to_f32(c.y[1])), pk(syf, syf));
+                const f2x qy23 = add2(pk(to_f32(c.y[2]), to_f32(c.y[3])), pk(syf, syf));
+                const f2x nt = pk(-thr, -thr);
+                const bool c23 = __any_sync(0xffffffffu, c.x[2] >= T(0));
+                uint32_t cand = 0;   // bit 4i+j: pair (own i, neighbour slot j) passes the estimate
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (!(px[i] >= T(0))) continue;
-                        if (dx == 0 && dy == 0 && i == j) continue;
-                        const double ddx = __dsub_rn((double)px[i], ex), ddy = __dsub_rn((double)py[i], ey);
-                        const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
-                        const double t = __ddiv_rn(__dsub_rn(rr, sigma), dr);
-                        if (t >= 0.0 && t < (double)kHistBins) atomicAdd(&sh[(int)t], 1u);
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= 2 && !own23) continue;
+                    const f2x tx2 = pk(ox[i], ox[i]), ty2 = pk(oy[i], oy[i]);
+                    f2x z = zpair(tx2, ty2, qx01, qy01, nt);
+                    cand |= ((lo32(z) >> 31) << (4 * i)) | ((hi32(z) >> 31) << (4 * i + 1));
+                    if (c23) {
+                        z = zpair(tx2, ty2, qx23, qy23, nt);
+                        cand |= ((lo32(z) >> 31) << (4 * i + 2)) | ((hi32(z) >> 31) << (4 * i + 3));
                     }
+                }
+                // empty own slots are excluded (two empty slots sit one cell offset
+                // apart), and no disk is paired with itself
+                cand &= occupied;
+                if (dx == 0 && dy == 0) cand &= ~0x8421u;
+                while (cand) {
+                    const int b = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    const int i = b >> 2, j = b & 3;
+                    const double px = (double)pick(own.x, i), py = (double)pick(own.y, i);
+                    const double ex = __dadd_rn((double)pick(c.x, j), (double)dx * wxd);
+                    const double ey = __dadd_rn((double)pick(c.y, j), (double)dy * wyd);
+                    const double ddx = __dsub_rn(px, ex), ddy = __dsub_rn(py, ey);
+                    const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
+                    const double t = __ddiv_rn(__dsub_rn(rr, sigma), dr);
+                    if (t >= 0.0 && t < (double)kHistBins) atomicAdd(&sh[(int)t], 1u);
                 }
             }
         }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kHistBins; b += blockDim.x)
+    for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y)
         if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
 }
 
 // ---- launchers ---------------------------------------------------------------------
-template <typename T>
-void launch_subsweep_t(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k) {
-    k_subsweep<T><<<subsweep_grid(c.g), dim3(32, 4), 0, c.stream>>>(
-        c.g, reinterpret_cast<typename Vec<T>::T2*>(cells), draw, k, c.partial);
+inline dim3 set_grid(const Geometry& g, dim3 block) {
+    return dim3((unsigned)((g.hx + block.x - 1) / block.x), (unsigned)((g.hy + block.y - 1) / block.y), 4u);
 }
 
 template <typename T>
 void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
-    const long long blocks = (c.g.C + 255) / 256;
-    k_shift<T><<<(unsigned)blocks, 256, 0, c.stream>>>(
-        c.g, reinterpret_cast<const typename Vec<T>::T2*>(src), reinterpret_cast<typename Vec<T>::T2*>(dst), draw,
-        c.st);
+    const dim3 block(64, 4);
+    k_shift<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(src),
+                                                               reinterpret_cast<T*>(dst), draw, c.st);
 }
 
 template <typename T>
 void launch_hist_t(const LaunchCtx& c, const void* cells) {
-    long long blocks = (c.g.C + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_hist<T><<<(unsigned)blocks, 256, 0, c.stream>>>(c.g, reinterpret_cast<const typename Vec<T>::T2*>(cells),
-                                                      c.hist);
+    const dim3 block(32, 8);
+    k_hist<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), c.hist);
 }
 
 }  // namespace hdmc

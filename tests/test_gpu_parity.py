@@ -201,7 +201,7 @@ def test_set_positions_and_errors(prec):
     bad[1] = bad[0] + [0.5, 0.0]
     bad[1] %= L
     with pytest.raises(hdmc.HDMCError) as e:
-        g.sys_set = hdmc.hdmc_set_positions(g.h, bad)
+        hdmc.hdmc_set_positions(g.h, bad)
     assert e.value.code == hdmc.HDMC_EOVERLAP
     _same(g, r, "state kept after a rejected set_positions")
     with pytest.raises(hdmc.HDMCError) as e:
@@ -258,3 +258,14 @@ def test_invariants_on_gpu_fp32_long_run():
     assert xy.min() >= 0 and xy[:, 0].max() < bx and xy[:, 1].max() < by
     pairs = cKDTree(xy, boxsize=[bx, by]).query_pairs(1.0 - 1e-6)
     assert len(pairs) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nsel", [1, 12, 20])
+def test_trials_per_cell(prec, nsel):
+    # n_M = 1 and n_M above the 8 directions drawn ahead per block of work
+    w = W.n1024_phi070()
+    g, r = _pair(w, prec, nsel=nsel, seed=4)
+    g.sweep(25)
+    r.sweep(25)
+    _same(g, r)

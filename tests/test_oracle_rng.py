@@ -119,11 +119,6 @@ def test_symmetric_variates_exact_mirror():
         assert -1.0 < u < 1.0
         m = u * 2.0**52
         assert m == math.floor(m) and int(m) % 2 == 1
-        w = hi
-        f = L.orc_sym23(w)
-        assert L.orc_sym23(w ^ 0xFFFFFFFF) == -f
-        mf = f * 2.0**23
-        assert mf == math.floor(mf) and int(mf) % 2 == 1 and -1.0 < f < 1.0
     # extremes of the lattice
     assert L.orc_sym52(0, 0) == -(1 - 2.0**-52)
     assert L.orc_sym52(0xFFFFFFFF, 0xFFFFFFFF) == 1 - 2.0**-52
@@ -145,9 +140,39 @@ def test_displacement_uniform_in_unit_disk(prec):
     assert abs(uv[:, 0].mean()) < 5 * 0.5 / math.sqrt(len(uv))
 
 
+@pytest.mark.parametrize("rng_range", [2, 6, 24])
+def test_bounded_21bit_fields_exactly_uniform(rng_range):
+    counts = O.lemire21_exhaustive(rng_range)
+    assert len(set(int(c) for c in counts)) == 1
+    assert int(counts[0]) == (2**21) // rng_range
+
+
+def test_21bit_fields_and_variates():
+    L = O.lib()
+    rng = np.random.default_rng(12)
+    for _ in range(2000):
+        w = rng.integers(0, 2**32, 4, dtype=np.uint64)
+        big = int(w[0]) | int(w[1]) << 32 | int(w[2]) << 64 | int(w[3]) << 96
+        f = O.fields21(w)
+        assert [int(x) for x in f] == [(big >> (21 * j)) & 0x1FFFFF for j in range(6)]
+    for k in range(0, 2**21, 997):
+        u = L.orc_sym21(k)
+        assert L.orc_sym21(k ^ 0x1FFFFF) == -u and -1 < u < 1
+        assert (u * 2**21) % 2 == 1
+    assert L.orc_sym21(0) == -(1 - 2.0**-21)
+
+
 @pytest.mark.parametrize("n", [2, 3, 4])
-def test_fisher_yates_uniform_permutations(n):
-    perms = O.shuffles(17, 3, 2, n, 120000)
+def test_permutation_decode_is_a_bijection(n):
+    seen = {tuple(int(x) for x in O.decode_perm(n, k)) for k in range(math.factorial(n))}
+    assert len(seen) == math.factorial(n)
+    assert all(sorted(p) == list(range(n)) for p in seen)
+
+
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_fisher_yates_uniform_permutations(n, prec):
+    perms = O.shuffles(17, 3, 2, n, 120000, prec)
     assert np.all(np.sort(perms, axis=1) == np.arange(n))
     code = np.zeros(len(perms), dtype=np.int64)
     for j in range(n):
