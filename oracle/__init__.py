@@ -85,6 +85,7 @@ def lib():
             "orc_decode_perm": (None, [ctypes.c_int, ctypes.c_uint32, _i32p]),
             "orc_visit_sequence": (None, [ctypes.c_int, ctypes.c_int, _i32p]),
             "orc_local_overlaps": (ctypes.c_int, [vp]),
+            "orc_edges2": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _f64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -204,6 +205,12 @@ def visit_sequence(n, nsel):
     out = np.zeros(nsel, dtype=np.int32)
     lib().orc_visit_sequence(n, nsel, _p(out, _i32p))
     return out
+
+
+def squared_bin_edges(sigma, dr, nbins):
+    E = np.zeros(nbins + 1, dtype=np.float64)
+    lib().orc_edges2(sigma, dr, nbins, _p(E, _f64p))
+    return E
 
 
 def set_threads(n):

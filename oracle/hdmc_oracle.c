@@ -1018,6 +1018,31 @@ void orc_positions(const oracle_t *o, double *xy)
 /* taken in cell-local frames over the 5x5 cell neighbourhood (w >= sigma,   */
 /* so two rings reach past sigma + c for c <= sigma), in binary64.          */
 /* ------------------------------------------------------------------------ */
+/* Bin of a squared distance r2: bin b covers [E_b, E_{b+1}) with the squared
+ * edges E_k = e_k * e_k, e_k = sigma + k*dr (each product and sum rounded
+ * once in binary64); -1 outside [E_0, E_nbins). */
+static int bin_of_r2(double r2, double sigma, double dr, int nbins)
+{
+    double e0 = sigma;
+    if (!(r2 >= e0 * e0)) return -1;
+    double en = sigma + (double)nbins * dr;
+    if (!(r2 < en * en)) return -1;
+    int b = 0;
+    for (int k = 1; k < nbins; ++k) {
+        double e = sigma + (double)k * dr;
+        if (r2 >= e * e) b = k;
+    }
+    return b;
+}
+
+void orc_edges2(double sigma, double dr, int nbins, double *E)
+{
+    for (int k = 0; k <= nbins; ++k) {
+        double e = sigma + (double)k * dr;
+        E[k] = e * e;
+    }
+}
+
 void orc_histogram(const oracle_t *o, int nbins, double dr, uint64_t *hist)
 {
     memset(hist, 0, sizeof(uint64_t) * (size_t)nbins);
@@ -1041,9 +1066,8 @@ void orc_histogram(const oracle_t *o, int nbins, double dr, uint64_t *hist)
                             double qx, qy;
                             slot_get(o, nc, j, &qx, &qy);
                             double ddx = px - (qx + sx), ddy = py - (qy + sy);
-                            double r = sqrt(ddx * ddx + ddy * ddy);
-                            double t = (r - sigma) / dr;
-                            if (t >= 0.0 && t < (double)nbins) hist[(int)t] += 1;
+                            int b = bin_of_r2(ddx * ddx + ddy * ddy, sigma, dr, nbins);
+                            if (b >= 0) hist[b] += 1;
                         }
                     }
             }
@@ -1085,9 +1109,8 @@ void orc_bruteforce_histogram(const double *xy, int64_t N, double Lx, double Ly,
                     if (i == j && ix == 0 && iy == 0) continue;
                     double dx = xy[2 * i] - (xy[2 * j] + (double)ix * Lx);
                     double dy = xy[2 * i + 1] - (xy[2 * j + 1] + (double)iy * Ly);
-                    double r = sqrt(dx * dx + dy * dy);
-                    double t = (r - sigma) / dr;
-                    if (t >= 0.0 && t < (double)nbins) hist[(int)t] += 1;
+                    int b = bin_of_r2(dx * dx + dy * dy, sigma, dr, nbins);
+                    if (b >= 0) hist[b] += 1;
                 }
         }
 }

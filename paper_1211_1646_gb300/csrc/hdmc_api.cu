@@ -45,7 +45,7 @@ bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx,
 }
 
 struct Layout {
-    size_t cells, table, shift_table, state, partial, hist, total;
+    size_t cells, table, shift_table, state, partial, hist, edges, total;
     int nblocks;
 };
 
@@ -60,7 +60,8 @@ Layout make_layout(const Geometry& g, int prec) {
     L.nblocks = (int)(grid.x * grid.y);
     L.partial = align_up(sizeof(unsigned long long) * 4 * (size_t)L.nblocks);
     L.hist = align_up(sizeof(unsigned long long) * kHistBins);
-    L.total = 2 * L.cells + L.table + L.shift_table + L.state + L.partial + L.hist;
+    L.edges = align_up(sizeof(double) * (kHistBins + 1));
+    L.total = 2 * L.cells + L.table + L.shift_table + L.state + L.partial + L.hist + L.edges;
     return L;
 }
 
@@ -89,6 +90,7 @@ struct hdmc_handle {
     DevState* st = nullptr;
     unsigned long long* partial = nullptr;
     unsigned long long* hist = nullptr;
+    double* edges2 = nullptr;
     uint64_t sweeps = 0, shifts = 0;
     int64_t n_samples = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (sweeps, parity) -> graph
@@ -100,6 +102,7 @@ struct hdmc_handle {
         c.st = st;
         c.partial = partial;
         c.hist = hist;
+        c.edges2 = edges2;
         return c;
     }
     void drop_graphs() {
@@ -500,8 +503,20 @@ int hdmc_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, dou
     h->partial = (unsigned long long*)p;
     p += h->lay.partial;
     h->hist = (unsigned long long*)p;
+    p += h->lay.hist;
+    h->edges2 = (double*)p;
 
     e = cuda_code(cudaMemset(h->ws + 2 * h->lay.cells, 0, h->lay.total - 2 * h->lay.cells));
+    if (!e) {
+        // squared histogram bin edges (sigma + k dr)^2, each rounded once
+        double E[kHistBins + 1];
+        const double dr = kHistDr * sigma;
+        for (int k = 0; k <= kHistBins; ++k) {
+            const double edge = sigma + (double)k * dr;
+            E[k] = edge * edge;
+        }
+        e = cuda_code(cudaMemcpy(h->edges2, E, sizeof(E), cudaMemcpyHostToDevice));
+    }
     int64_t nx, ny;
     if (!e && !lattice_shape(N, Lx, Ly, nx, ny)) e = HDMC_EINVAL;
     if (!e) {

@@ -7,10 +7,10 @@
 // stream, block b of which is Philox(key, (c0, c1, c2, b)):
 //   sweep-level draws of sweep s (Alg. 1 lines 2, 15-16):
 //                      (s, 0xFFFFFFFF, 2<<28)
-//   particle shuffle of cell c in sweep s, set Q (Alg. 1 line 5):
+//   trial stream of the update of cell c in sweep s, set Q (Alg. 1 lines
+//   5 and 8):          (s, c, (1<<28)|(Q<<24))
+//   shuffle stream of that update (binary64 shuffles; binary32 fallback):
 //                      (s, c, (0<<28)|(Q<<24))
-//   trial t of cell c in sweep s, set Q (Alg. 1 line 8):
-//                      (s, c, (1<<28)|(Q<<24)|t)
 //   start jitter of disk p:  (p, 0xFFFFFFFE, 3<<28)
 //   explicit extra shift k:  (k, 0xFFFFFFFF, 4<<28)
 // with c = cy*mx + cx the canonical cell number.  Because the streams are
@@ -137,12 +137,6 @@ __host__ __device__ inline double sym52(uint32_t hi, uint32_t lo) {
     return (double)m * 0x1p-52;
 }
 
-// Odd multiples of 2^-23 in (-1,1) from the top 23 bits of one word.
-__host__ __device__ inline float sym23(uint32_t w) {
-    const int32_t m = (int32_t)(2 * (w >> 9) + 1) - (1 << 23);
-    return (float)m * 0x1p-23f;
-}
-
 __host__ __device__ inline double unif53(uint32_t hi, uint32_t lo) {
     const uint64_t k = (((uint64_t)hi << 32) | lo) >> 11;
     return (double)k * 0x1p-53;
@@ -182,6 +176,7 @@ struct LaunchCtx {
     DevState* st;
     unsigned long long* partial;   // per-block trial counters, 4 per sub-sweep block
     unsigned long long* hist;      // contact histogram accumulator (kHistBins)
+    const double* edges2;          // squared bin edges (sigma + k dr)^2, k = 0..kHistBins
 };
 
 void launch_draws(const LaunchCtx& c, SweepDraw* table, int count, bool sweep_mode);

@@ -259,6 +259,11 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
             n2[c] = __ldg(p + 2);
         }
     }
+    // first block of the cell's trial stream (independent of the loads in flight)
+    const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+    const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
+    uint32_t F[6];
+    fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
     const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
     uint32_t dir23 = 0;   // warp-uniform: directions where some lane has a third disk
 #pragma unroll
@@ -267,11 +272,7 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
 
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
     if (n > 0) {
-        const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
-        const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
         uint32_t blk = 0;
-        uint32_t F[6];
-        fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
         // shuffle (Alg. 1 line 5): one draw in [0, n!) by 21-bit Lemire on field 0
         if (n >= 2) {
             const uint32_t range = factorial(n);
@@ -293,6 +294,18 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
             const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
             qx01[c] = add2(pk(n01[c].x, n01[c].y), pk(sx, sx));
             qy01[c] = add2(pk(n01[c].z, n01[c].w), pk(sy, sy));
+        }
+        // slot pair (2,3) of the first flagged direction, translated; further
+        // flagged directions (rare) are read in the trial loop
+        f2x fx23 = 0, fy23 = 0;
+        const uint32_t more23 = dir23 & (dir23 - 1);
+        if (dir23) {
+            const int c = __ffs(dir23) - 1;
+            const float2* p = reinterpret_cast<const float2*>(cells + 8 * nbh.index(g, c, hx, hy));
+            const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
+            const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
+            fx23 = add2(pk(x23.x, x23.y), pk(sx, sx));
+            fy23 = add2(pk(y23.x, y23.y), pk(sy, sy));
         }
         const float df = g.df;
         const f2x ns2 = pk(-g.sig2f, -g.sig2f);
@@ -337,7 +350,11 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
                     z = zpair(tx2, ty2, qx01[c], qy01[c], ns2);
                     acc |= lo32(z) | hi32(z);
                 }
-                for (uint32_t m = dir23; m; m &= m - 1) {   // warp-uniform, rarely taken
+                if (dir23) {
+                    z = zpair(tx2, ty2, fx23, fy23, ns2);
+                    acc |= lo32(z) | hi32(z);
+                }
+                for (uint32_t m = more23; m; m &= m - 1) {   // warp-uniform, rarely taken
                     const int c = __ffs(m) - 1;
                     const float2* p = reinterpret_cast<const float2*>(cells + 8 * nbh.index(g, c, hx, hy));
                     const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
@@ -362,83 +379,196 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
 // ---- binary64 sub-sweep ---------------------------------------------------------------
 // Same algorithm in binary64.  Draws: shuffle by one 32-bit Lemire draw in
 // [0, n!) from the cell's shuffle stream; trial t takes the t-th kept attempt
-// of the trial stream, attempt a = block a.
-static __global__ void __launch_bounds__(128)
+// of the trial stream, attempt a = block a: u = sym52(w0,w1), v = sym52(w2,w3),
+// kept iff u*u + v*v < 1.
+//
+// Every decision is the exact binary64 expression, but binary64 arithmetic
+// is slow on this GPU, so binary32 estimates settle the clear cases first:
+//  - in-circle test: u, v truncated to 23 bits (|error| <= 2^-23); cases with
+//    the estimate of u^2 + v^2 within 2^-18 of 1 are decided in binary64;
+//  - overlap test: positions truncated to binary32 (relative error <= 2^-23),
+//    the squared distance estimated with binary32 pair arithmetic (error
+//    below 3e-6 where it matters, r^2 < 1.3); a candidate counts as certainly
+//    overlapping below sigma^2 - 2^-15 and certainly clear above sigma^2 + 2^-15;
+//    if any candidate falls in between, all candidates are tested in binary64.
+constexpr float kOverlapBand = 0x1p-15f;
+constexpr float kCircleBand = 0x1p-18f;
+
+__device__ __forceinline__ bool exact_trial_hit(const Geometry& g, const double* __restrict__ cells,
+                                                  const Neighbourhood& nbh, int hx, int hy, const Cell<double>& own,
+                                                  int i, double tx, double ty) {
+    bool hit = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double ddx = __dsub_rn(tx, own.x[j]), ddy = __dsub_rn(ty, own.y[j]);
+        hit |= (j != i) && (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2);
+    }
+    for (int c = 0; c < 8; ++c) {
+        Cell<double> a;
+        load_cell_ro(cells + 8 * nbh.index(g, c, hx, hy), a);
+        const double sx = (double)dir_dx(c) * g.wx, sy = (double)dir_dy(c) * g.wy;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double ddx = __dsub_rn(tx, __dadd_rn(a.x[j], sx)), ddy = __dsub_rn(ty, __dadd_rn(a.y[j], sy));
+            hit |= __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2;
+        }
+    }
+    return hit;
+}
+
+// 53-bit odd integer m of sym52 (u = m 2^-52) and its binary32 truncation m 2^-52.
+__device__ __forceinline__ long long sym52_int(uint32_t hi, uint32_t lo) {
+    const unsigned long long k = (((unsigned long long)hi << 32) | lo) >> 12;
+    return (long long)(2 * k + 1) - (1ll << 52);
+}
+__device__ __forceinline__ float sym52_est(long long m) { return (float)(int)(m >> 29) * 0x1p-23f; }
+
+static __global__ void __launch_bounds__(128, 3)
 k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
     const int Q = draw->perm[k];
     const uint32_t sweep = draw->sweep;
-    const int qx = Q & 1, qy = Q >> 1;
     const int hx = blockIdx.x * 32 + threadIdx.x;
     const int hy = blockIdx.y * 4 + threadIdx.y;
+    const bool live = hx < g.hx && hy < g.hy;
+    const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
+    const Neighbourhood nbh(g, Q, hx, hy);
+
+    Cell<double> own;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = kEmpty;
+    double* ownp = cells + 8 * (nbh.base[0] + (long long)hy * g.hx + hx);
+    if (live) load_cell(ownp, own);
+    float4 n01[8];   // binary32 truncations of neighbour slots 0,1 (x0 x1 y0 y1)
+    float n2[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        n01[c] = make_float4((float)kEmpty, (float)kEmpty, (float)kEmpty, (float)kEmpty);
+        n2[c] = (float)kEmpty;
+        if (live) {
+            const double* p = cells + 8 * nbh.index(g, c, hx, hy);
+            const double2 x01 = __ldg(reinterpret_cast<const double2*>(p));
+            const double2 y01 = __ldg(reinterpret_cast<const double2*>(p) + 2);
+            n01[c] = make_float4(approx_f32(x01.x), approx_f32(x01.y), approx_f32(y01.x), approx_f32(y01.y));
+            n2[c] = approx_f32(__ldg(p + 2));
+        }
+    }
+    const int n = (own.x[0] >= 0.0) + (own.x[1] >= 0.0) + (own.x[2] >= 0.0) + (own.x[3] >= 0.0);
+    uint32_t dir23 = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dir23 |= __any_sync(0xffffffffu, n2[c] >= 0.f) ? (1u << c) : 0u;
+    const bool own23 = __any_sync(0xffffffffu, n >= 3);
+
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
-    if (hx < g.hx && hy < g.hy) {
-        const int cx = 2 * hx + qx, cy = 2 * hy + qy;
-        double* ownp = cells + 8 * ((long long)Q * g.cq + (long long)hy * g.hx + hx);
-        Cell<double> own;
-        load_cell(ownp, own);
-        const int n = (own.x[0] >= 0.0) + (own.x[1] >= 0.0) + (own.x[2] >= 0.0) + (own.x[3] >= 0.0);
-        if (n > 0) {
-            const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
-            const uint32_t setbits = (uint32_t)Q << 24;
-            if (n >= 2) {
-                WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
-                const uint32_t pk = perm_from_index(n, s.bounded(factorial(n)));
-                permute(own.x, pk);
-                permute(own.y, pk);
+    if (n > 0) {
+        const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+        const uint32_t setbits = (uint32_t)Q << 24;
+        if (n >= 2) {
+            WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
+            const uint32_t pk = perm_from_index(n, s.bounded(factorial(n)));
+            permute(own.x, pk);
+            permute(own.y, pk);
+        }
+        float ofx[4], ofy[4];   // binary32 truncations of the own slots
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ofx[j] = approx_f32(own.x[j]);
+            ofy[j] = approx_f32(own.y[j]);
+        }
+        const float wxf = (float)g.wx, wyf = (float)g.wy;
+        f2x qx01[8], qy01[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float sx = (float)dir_dx(c) * wxf, sy = (float)dir_dy(c) * wyf;
+            qx01[c] = add2(pk(n01[c].x, n01[c].y), pk(sx, sx));
+            qy01[c] = add2(pk(n01[c].z, n01[c].w), pk(sy, sy));
+        }
+        f2x fx23 = 0, fy23 = 0;
+        const uint32_t more23 = dir23 & (dir23 - 1);
+        if (dir23) {
+            const int c = __ffs(dir23) - 1;
+            const double2* p = reinterpret_cast<const double2*>(cells + 8 * nbh.index(g, c, hx, hy));
+            const double2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
+            const float sx = (float)dir_dx(c) * wxf, sy = (float)dir_dy(c) * wyf;
+            fx23 = add2(pk(approx_f32(x23.x), approx_f32(x23.y)), pk(sx, sx));
+            fy23 = add2(pk(approx_f32(y23.x), approx_f32(y23.y)), pk(sy, sy));
+        }
+        const float s2f = (float)g.sig2;
+        const f2x nlo = pk(-(s2f - kOverlapBand), -(s2f - kOverlapBand));   // certainly overlapping below
+        const f2x nhi = pk(-(s2f + kOverlapBand), -(s2f + kOverlapBand));   // possibly overlapping below
+        const double dscaled = g.d * 0x1p-52;   // d*u = (d 2^-52) * m exactly as real numbers
+        const uint32_t c2 = (kDomTrial << 28) | setbits;
+        uint32_t blk = 0;
+        int i = 0;
+        for (int t = 0; t < g.nsel; ++t) {
+            long long mu, mv;
+            for (;;) {
+                const uint4 r = philox4x32_10(make_uint4(sweep, cell, c2, blk++), g.key0, g.key1);
+                mu = sym52_int(r.x, r.y);
+                mv = sym52_int(r.z, r.w);
+                const float uf = sym52_est(mu), vf = sym52_est(mv);
+                const float e = __fmaf_rn(uf, uf, __fmul_rn(vf, vf));
+                if (e < 1.0f - kCircleBand) break;
+                if (e >= 1.0f + kCircleBand) continue;
+                const double u = (double)mu * 0x1p-52, v = (double)mv * 0x1p-52;
+                if (__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) < 1.0) break;
             }
-            double qxs[32], qys[32];
+            const double tx = __dadd_rn(pick(own.x, i), __dmul_rn(dscaled, (double)mu));
+            const double ty = __dadd_rn(pick(own.y, i), __dmul_rn(dscaled, (double)mv));
+            const bool inside = tx >= 0.0 && tx < g.wx && ty >= 0.0 && ty < g.wy;
+            const float txf = approx_f32(tx), tyf = approx_f32(ty);
+            const f2x tx2 = pk(txf, txf), ty2 = pk(tyf, tyf);
+            uint32_t sure = 0, maybe = 0;   // sign bits: certainly / possibly overlapping
+            {
+                const f2x dx = sub2(tx2, pk(ofx[0], ofx[1])), dy = sub2(ty2, pk(ofy[0], ofy[1]));
+                const f2x zl = fma2(dx, dx, fma2(dy, dy, nlo)), zh = fma2(dx, dx, fma2(dy, dy, nhi));
+                sure |= (i == 0 ? 0u : lo32(zl)) | (i == 1 ? 0u : hi32(zl));
+                maybe |= (i == 0 ? 0u : lo32(zh)) | (i == 1 ? 0u : hi32(zh));
+            }
+            if (own23) {
+                const f2x dx = sub2(tx2, pk(ofx[2], ofx[3])), dy = sub2(ty2, pk(ofy[2], ofy[3]));
+                const f2x zl = fma2(dx, dx, fma2(dy, dy, nlo)), zh = fma2(dx, dx, fma2(dy, dy, nhi));
+                sure |= (i == 2 ? 0u : lo32(zl)) | (i == 3 ? 0u : hi32(zl));
+                maybe |= (i == 2 ? 0u : lo32(zh)) | (i == 3 ? 0u : hi32(zh));
+            }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const int dx = (c < 3) ? c - 1 : (c == 3 ? -1 : (c == 4 ? 1 : c - 6));
-                const int dy = (c < 3) ? -1 : (c < 5 ? 0 : 1);
-                Cell<double> a;
-                load_cell_ro(cells + 8 * storage_index(g, wrap(cx + dx, g.mx), wrap(cy + dy, g.my)), a);
-                const double sx = (double)dx * g.wx, sy = (double)dy * g.wy;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    qxs[4 * c + j] = __dadd_rn(a.x[j], sx);
-                    qys[4 * c + j] = __dadd_rn(a.y[j], sy);
-                }
+                const f2x dx = sub2(tx2, qx01[c]), dy = sub2(ty2, qy01[c]);
+                const f2x zl = fma2(dx, dx, fma2(dy, dy, nlo)), zh = fma2(dx, dx, fma2(dy, dy, nhi));
+                sure |= lo32(zl) | hi32(zl);
+                maybe |= lo32(zh) | hi32(zh);
             }
-            uint32_t blk = 0;
-            const uint32_t c2 = (kDomTrial << 28) | setbits;
-            int i = 0;
-            for (int t = 0; t < g.nsel; ++t) {
-                double u, v;
-                for (;;) {
-                    const uint4 r = philox4x32_10(make_uint4(sweep, cell, c2, blk++), g.key0, g.key1);
-                    u = sym52(r.x, r.y);
-                    v = sym52(r.z, r.w);
-                    if (__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) < 1.0) break;
-                }
-                const double tx = __dadd_rn(pick(own.x, i), __dmul_rn(g.d, u));
-                const double ty = __dadd_rn(pick(own.y, i), __dmul_rn(g.d, v));
-                ++n_tr;
-                if (tx >= 0.0 && tx < g.wx && ty >= 0.0 && ty < g.wy) {
-                    bool hit = false;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const double ddx = __dsub_rn(tx, own.x[j]), ddy = __dsub_rn(ty, own.y[j]);
-                        hit |= (j != i) && (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const double ddx = __dsub_rn(tx, qxs[j]), ddy = __dsub_rn(ty, qys[j]);
-                        hit |= __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2;
-                    }
-                    if (!hit) {
-                        put_if(own.x, i, tx, true);
-                        put_if(own.y, i, ty, true);
-                        ++n_acc;
-                    }
-                } else {
-                    ++n_leave;
-                }
-                i = (i + 1 == n) ? 0 : i + 1;
+            if (dir23) {
+                const f2x dx = sub2(tx2, fx23), dy = sub2(ty2, fy23);
+                const f2x zl = fma2(dx, dx, fma2(dy, dy, nlo)), zh = fma2(dx, dx, fma2(dy, dy, nhi));
+                sure |= lo32(zl) | hi32(zl);
+                maybe |= lo32(zh) | hi32(zh);
             }
-            store_cell(ownp, own);
+            for (uint32_t m = more23; m; m &= m - 1) {
+                const int c = __ffs(m) - 1;
+                const double2* p = reinterpret_cast<const double2*>(cells + 8 * nbh.index(g, c, hx, hy));
+                const double2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
+                const float sx = (float)dir_dx(c) * wxf, sy = (float)dir_dy(c) * wyf;
+                const f2x dx = sub2(tx2, add2(pk(approx_f32(x23.x), approx_f32(x23.y)), pk(sx, sx)));
+                const f2x dy = sub2(ty2, add2(pk(approx_f32(y23.x), approx_f32(y23.y)), pk(sy, sy)));
+                const f2x zl = fma2(dx, dx, fma2(dy, dy, nlo)), zh = fma2(dx, dx, fma2(dy, dy, nhi));
+                sure |= lo32(zl) | hi32(zl);
+                maybe |= lo32(zh) | hi32(zh);
+            }
+            bool hit = (sure & 0x80000000u) != 0;
+            if (inside && !hit && (maybe & 0x80000000u))
+                hit = exact_trial_hit(g, cells, nbh, hx, hy, own, i, tx, ty);
+            const bool ok = inside && !hit;
+            put_if(own.x, i, tx, ok);
+            put_if(own.y, i, ty, ok);
+            put_if(ofx, i, txf, ok);
+            put_if(ofy, i, tyf, ok);
+            ++n_tr;
+            n_acc += ok;
+            n_leave += !inside;
+            i = (i + 1 == n) ? 0 : i + 1;
         }
+        store_cell(ownp, own);
     }
     add_block_counters(n_tr, n_acc, n_leave, partial);
 }
@@ -533,21 +663,25 @@ k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const 
 }
 
 // ---- contact histogram: Sec. 4 ------------------------------------------------------
-// Ordered pairs (i, j != i) at distance r in [sigma, sigma + 200 dr), bin
-// floor((r - sigma)/dr), the distance taken in binary64 from cell-local
-// coordinates over the 5x5 neighbourhood (w >= sigma, so two rings reach past
-// 1.02 sigma).  A binary32 estimate of r^2 with a wide margin selects the
-// candidates; only those get the binary64 distance.  One thread per cell,
+// Ordered pairs (i, j != i) at distance r in [sigma, sigma + 200 dr), in bins
+// [sigma + b dr, sigma + (b+1) dr) decided on the binary64 r^2 against the
+// squared bin edges; distances from cell-local coordinates over the 5x5
+// neighbourhood (w >= sigma, so two rings reach past 1.02 sigma).  A binary32
+// estimate of r^2 with a wide margin selects the candidates; only those get
+// the binary64 distance.  One thread per cell,
 // grid (set row, set column, set); per-block shared histogram.
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return approx_f32(v); }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_hist(const Geometry g, const T* __restrict__ cells, unsigned long long* __restrict__ hist) {
+k_hist(const Geometry g, const T* __restrict__ cells, const double* __restrict__ edges2,
+       unsigned long long* __restrict__ hist) {
     __shared__ unsigned int sh[kHistBins];
+    __shared__ double sE[kHistBins + 1];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y) sh[b] = 0u;
+    for (int b = tid; b <= kHistBins; b += blockDim.x * blockDim.y) sE[b] = edges2[b];
     __syncthreads();
     const int hx = blockIdx.x * blockDim.x + threadIdx.x;
     const int hy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -563,8 +697,8 @@ k_hist(const Geometry g, const T* __restrict__ cells, unsigned long long* __rest
     if (any) {
         const double wxd = (double)Prm<T>::wx(g), wyd = (double)Prm<T>::wy(g);
         const float wxf = (float)Prm<T>::wx(g), wyf = (float)Prm<T>::wy(g);
-        const double sigma = g.sigma, dr = kHistDr * g.sigma;
-        const float rmax = (float)(g.sigma + kHistBins * dr);
+        const float sigf = (float)g.sigma, inv_drf = (float)(1.0 / (kHistDr * g.sigma));
+        const float rmax = (float)(g.sigma + kHistBins * kHistDr * g.sigma);
         const float thr = rmax * rmax * 1.001f;   // binary32 estimate margin (estimate error < 1e-6)
         float ox[4], oy[4];
         uint32_t occupied = 0;   // bits 4i..4i+3 set when own slot i holds a disk
@@ -611,9 +745,16 @@ k_hist(const Geometry g, const T* __restrict__ cells, unsigned long long* __rest
                     const double ex = __dadd_rn((double)pick(c.x, j), (double)dx * wxd);
                     const double ey = __dadd_rn((double)pick(c.y, j), (double)dy * wyd);
                     const double ddx = __dsub_rn(px, ex), ddy = __dsub_rn(py, ey);
-                    const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
-                    const double t = __ddiv_rn(__dsub_rn(rr, sigma), dr);
-                    if (t >= 0.0 && t < (double)kHistBins) atomicAdd(&sh[(int)t], 1u);
+                    const double r2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+                    if (r2 >= sE[0] && r2 < sE[kHistBins]) {
+                        // bin b: sE[b] <= r2 < sE[b+1]; start from a binary32 estimate
+                        const float r2f = approx_f32(r2);
+                        int bb = (int)((r2f * rsqrtf(r2f) - sigf) * inv_drf);
+                        bb = bb < 0 ? 0 : (bb > kHistBins - 1 ? kHistBins - 1 : bb);
+                        while (bb > 0 && r2 < sE[bb]) --bb;
+                        while (bb < kHistBins - 1 && r2 >= sE[bb + 1]) ++bb;
+                        atomicAdd(&sh[bb], 1u);
+                    }
                 }
             }
         }
@@ -638,7 +779,8 @@ void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepD
 template <typename T>
 void launch_hist_t(const LaunchCtx& c, const void* cells) {
     const dim3 block(32, 8);
-    k_hist<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), c.hist);
+    k_hist<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), c.edges2,
+                                                              c.hist);
 }
 
 }  // namespace hdmc

@@ -282,9 +282,11 @@ def _pair_histogram_kdtree(xy, L, sigma, nbins, dr):
     pairs = t.query_pairs(sigma + nbins * dr, output_type="ndarray")
     d = xy[pairs[:, 0]] - xy[pairs[:, 1]]
     d -= L * np.round(d / L)
-    r = np.hypot(d[:, 0], d[:, 1])
-    b = np.floor((r - sigma) / dr)
-    b = b[(b >= 0) & (b < nbins)].astype(int)
+    r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+    e = sigma + np.arange(nbins + 1) * dr
+    E = e * e
+    keep = (r2 >= E[0]) & (r2 < E[-1])
+    b = np.searchsorted(E, r2[keep], side="right") - 1
     return 2 * np.bincount(b, minlength=nbins)
 
 
@@ -301,6 +303,14 @@ def test_ideal_gas_contact_value_is_one():
     assert abs(g.mean() - 1) < 4 / math.sqrt(hist.sum() / 2)
     g0 = P.contact_value(R, g, 1.0, 0.02)
     assert abs(g0 - 1) < 4 * 6 / math.sqrt(hist.sum() / 2)
+
+
+def test_squared_bin_edges():
+    # bin b covers [sigma + b dr, sigma + (b+1) dr): its squared edges are
+    # increasing and within rounding of the exact squares
+    E = O.squared_bin_edges(1.0, 1e-4, 200)
+    exact = (1.0 + 1e-4 * np.arange(201)) ** 2
+    assert np.all(np.diff(E) > 0) and np.allclose(E, exact, rtol=1e-15, atol=0)
 
 
 def test_bruteforce_histogram_matches_kdtree():
