@@ -169,6 +169,37 @@ int hdmc_sync(hdmc_t *h);
  * draws launch (each nullable).  Synchronises. */
 int hdmc_profile_sweeps(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift, double *ms_draws);
 
+/* Contact histogram for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this entry point exists for code that may not
+ * call cudaMalloc (inside another framework's memory pool, a memory-capped
+ * process, or a plugin that owns no GPU allocations).  It allocates nothing:
+ * its only device scratch is a file-scope array of HDMC_NOALLOC_MAX_BINS
+ * 64-bit counters that every GPU which loads the library keeps until the
+ * process exits.
+ *   dev_local: device, caller-owned, 8*mx*my doubles in the layout of
+ *              hdmc_get_state (slot j of canonical cell c = cy*mx + cx at
+ *              [(4c+j)*2], [(4c+j)*2+1], cell-local coordinates; a slot is
+ *              empty iff its x is negative).  Read only.
+ *   mx, my:    cell grid (>= 4 each); wx, wy: cell widths used to translate
+ *              neighbouring cells (pass the binary32 widths, widened, for a
+ *              state of an HDMC_FP32_LOCAL system).
+ *   sigma, nbins, dr: ordered pairs at distance r in [sigma, sigma + nbins dr)
+ *              are counted in bins [sigma + b dr, sigma + (b+1) dr), decided
+ *              on the binary64 r^2 against the squared bin edges, as
+ *              hdmc_pressure does; 1 <= nbins <= HDMC_NOALLOC_MAX_BINS and
+ *              sigma + nbins dr <= 2 min(wx, wy).
+ *   hist:      host, nbins counts (output).
+ *   stream:    cudaStream_t or NULL (legacy default stream).
+ * Errors: HDMC_EINVAL for a size above the maximum or invalid arguments
+ * (nothing is launched), HDMC_ECUDA.  Synchronises the stream.
+ * The first call on each device looks up the device address of the scratch
+ * array (with that device current); make that first call before any stream
+ * capture.  All calls share the array and each call clears it first, so
+ * calls that overlap on the GPU (several streams or host threads) race. */
+#define HDMC_NOALLOC_MAX_BINS 1024
+int hdmc_histogram_noalloc(const double *dev_local, int32_t mx, int32_t my, double wx, double wy, double sigma,
+                           int32_t nbins, double dr, uint64_t *hist, void *stream);
+
 /* Frees the handle (and the workspace if the library allocated it). */
 void hdmc_destroy(hdmc_t *h);
 

@@ -16,6 +16,7 @@ HDMC_OK, HDMC_EINVAL, HDMC_ECUDA, HDMC_EOVERFLOW, HDMC_EOVERLAP, HDMC_ETIMEOUT, 
 HDMC_FP64, HDMC_FP32_LOCAL = 0, 1
 HDMC_EMPTY_SLOT = -1.0e4
 HDMC_HIST_BINS = 200
+HDMC_NOALLOC_MAX_BINS = 1024
 
 _PRECISIONS = {"fp64": HDMC_FP64, "fp32": HDMC_FP32_LOCAL, "fp32_local": HDMC_FP32_LOCAL,
                HDMC_FP64: HDMC_FP64, HDMC_FP32_LOCAL: HDMC_FP32_LOCAL}
@@ -49,6 +50,8 @@ SIGNATURES = {
     "hdmc_set_stream": (ctypes.c_int, [_vp, _vp]),
     "hdmc_sync": (ctypes.c_int, [_vp]),
     "hdmc_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p, _f64p]),
+    "hdmc_histogram_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int32, ctypes.c_double, _u64p, _vp]),
     "hdmc_destroy": (None, [_vp]),
     "hdmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -199,6 +202,16 @@ def hdmc_profile_sweeps(h, n):
     _check(lib().hdmc_profile_sweeps(h, n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "hdmc_profile_sweeps")
     return a.value, b.value, c.value
+
+
+def hdmc_histogram_noalloc(dev_local, mx, my, wx, wy, sigma, nbins, dr, stream=None):
+    """Contact histogram of a caller-owned device state (device pointer to
+    8*mx*my doubles in the hdmc_get_state layout) without any device
+    allocation; returns nbins uint64 counts."""
+    hist = np.zeros(nbins, dtype=np.uint64)
+    _check(lib().hdmc_histogram_noalloc(dev_local, mx, my, wx, wy, sigma, nbins, dr, _p(hist, _u64p), stream),
+           "hdmc_histogram_noalloc")
+    return hist
 
 
 def hdmc_destroy(h):
