@@ -169,6 +169,75 @@ int hdmc_sync(hdmc_t *h);
  * draws launch (each nullable).  Synchronises. */
 int hdmc_profile_sweeps(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift, double *ms_draws);
 
+/* ---- batched replicas ----------------------------------------------------
+ * R independent systems advanced together: every stage of a sweep is one
+ * launch over all replicas, recorded into CUDA graphs, so small systems share
+ * the GPU instead of each launching its own kernels.  Replica r is exactly the
+ * system hdmc_create(N[r], Lx[r], Ly[r], sigma, d[r], nselect[r], seeds[r],
+ * precision, ...) would build and its trajectory is bit-identical to that
+ * run (the random streams are keyed by the replica's seed); batching only
+ * changes the launch layout. */
+typedef struct hdmc_batch_handle hdmc_batch_t;
+
+/* Device bytes for a batch (0 if a replica's parameters are invalid). */
+size_t hdmc_batch_workspace_bytes(int R, const int64_t *N, const double *Lx, const double *Ly, double sigma,
+                                  int precision);
+
+/* Creates R replicas (1 <= R <= 65535); N, Lx, Ly, d, seeds: host arrays of
+ * length R with the meaning of hdmc_create's arguments; nselect: host array
+ * of length R or NULL (4 for every replica).  dev_workspace / stream as in
+ * hdmc_create.  Errors as hdmc_create (the first failing replica decides).
+ * Synchronises. */
+int hdmc_batch_create(hdmc_batch_t **out, int R, const int64_t *N, const double *Lx, const double *Ly,
+                      double sigma, const double *d, const int32_t *nselect, const uint64_t *seeds, int precision,
+                      void *dev_workspace, size_t workspace_bytes, void *stream);
+
+/* Enqueues n sweeps of every replica (Algorithm 1). */
+int hdmc_batch_sweep(hdmc_batch_t *b, int64_t n);
+
+/* Enqueues the contact histogram of every replica into its accumulator. */
+int hdmc_batch_sample(hdmc_batch_t *b);
+
+/* Per-replica pressure from the accumulated samples, as hdmc_pressure:
+ * betaP_over_rho[R], g_contact[R], hist[R*HDMC_HIST_BINS] (each nullable).
+ * Clears the accumulators.  Synchronises. */
+int hdmc_batch_pressure(hdmc_batch_t *b, double *betaP_over_rho, double *g_contact, uint64_t *hist,
+                        int64_t *n_samples);
+
+/* Raw state of replica r in the layout of hdmc_get_state.  Synchronises. */
+int hdmc_batch_get_state(hdmc_batch_t *b, int r, double *local, uint8_t *counts);
+
+/* Per-replica trial counters out[4r + k], k as in hdmc_counters.  Synchronises. */
+int hdmc_batch_counters(hdmc_batch_t *b, uint64_t *out);
+
+/* Geometry of replica r, sweeps done, its grid origin (nullable outputs). */
+int hdmc_batch_info(hdmc_batch_t *b, int r, int32_t *mx, int32_t *my, double *wx, double *wy,
+                    uint64_t *sweeps_done, double origin[2]);
+
+/* Sets n_M of every replica (host array of R values in 1..255). */
+int hdmc_batch_set_nselect(hdmc_batch_t *b, const int32_t *nselect);
+
+/* Sets the sub-sweep block height (2, 4 or 8 rows of 32 active cells;
+ * binary32 batches only).  Results do not depend on it.  Synchronises. */
+int hdmc_batch_set_rows(hdmc_batch_t *b, int32_t rows_per_block);
+
+/* Current launch configuration: cells per block row count of the sub-sweep
+ * (block = 32 x rows active cells) and n_M of every replica (nselect[R]). */
+int hdmc_batch_config(hdmc_batch_t *b, int32_t *rows_per_block, int32_t *nselect);
+
+/* Autotuner (runs real sweeps, which advance every replica): picks the
+ * sub-sweep block height among 32x2, 32x4, 32x8 active cells by the time of
+ * `sweeps` recorded sweeps (binary32 batches), then n_M in {1, 2, 4, 8} (the
+ * same for every replica) maximising the net squared displacement per disk
+ * and second over `sweeps` sweeps, summed over replicas -- each disk's
+ * displacement is taken over its cell update, so confinement to the cell
+ * counts against a large n_M (the paper tunes n_M by an autocorrelation time
+ * per wall-clock second, Sec. 3.3).  1 <= sweeps <= 4096.  Synchronises. */
+int hdmc_batch_autotune(hdmc_batch_t *b, int64_t sweeps, int32_t *rows_per_block, int32_t *nselect_chosen);
+
+/* Frees the batch (and the workspace if the library allocated it). */
+void hdmc_batch_destroy(hdmc_batch_t *b);
+
 /* Contact histogram for callers that cannot allocate device memory.  The
  * paper has no counterpart: this entry point exists for code that may not
  * call cudaMalloc (inside another framework's memory pool, a memory-capped

@@ -33,6 +33,9 @@ constexpr int kFitDegree = 5;             // polynomial degree (Sec. 4)
 
 constexpr uint32_t kDomShuffle = 0u, kDomTrial = 1u, kDomSweep = 2u, kDomInit = 3u, kDomShift = 4u;
 
+constexpr int kShiftBX = 64, kShiftBY = 4;   // shift block: 64 set columns x 4 set rows of one set
+constexpr int kHistBX = 32, kHistBY = 8;     // histogram block: 32 set columns x 8 set rows of one set
+
 // Geometry and move parameters, passed by value to every kernel.
 struct Geometry {
     int mx, my;            // cells per axis, both even
@@ -67,6 +70,18 @@ struct DevState {
     double origin[2];                // accumulated grid origin (sum of f*ds)
     unsigned int error;              // bit 0: a cell received more than 4 disks
     unsigned int pad[3];
+};
+
+// One replica of a batch: its geometry, where its cells start in the batch
+// arena, and its share of each stage's launch (blocks of one replica are
+// contiguous in the flat block index).
+struct ReplicaDesc {
+    Geometry g;
+    long long cell_off;   // first cell of the replica in the arena
+    long long part_off;   // first sub-sweep counter slot of the replica
+    int sub_gx, sub_block0;           // sub-sweep: blocks per set row, first flat block
+    int sh_gx, sh_gy, sh_block0;      // shift: blocks per set row / column, first flat block
+    int hi_gx, hi_gy, hi_block0;      // histogram: same
 };
 
 // Cell storage: the cells of one checkerboard set are contiguous (set-major),
@@ -180,6 +195,7 @@ struct LaunchCtx {
 };
 
 void launch_draws(const LaunchCtx& c, SweepDraw* table, int count, bool sweep_mode);
+void launch_draws_batch(cudaStream_t s, const ReplicaDesc* reps, DevState* sts, SweepDraw* table, int R, int count);
 dim3 subsweep_grid(const Geometry& g);
 
 void launch_subsweep_f64(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k);
@@ -187,6 +203,27 @@ void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const Swee
 void launch_hist_f64(const LaunchCtx& c, const void* cells);
 
 void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k);
+
+// Batched stages (one launch over all R replicas).
+struct BatchCtx {
+    cudaStream_t stream;
+    const ReplicaDesc* reps;
+    const unsigned short* sub_map;
+    const unsigned short* sh_map;
+    const unsigned short* hi_map;
+    int sub_blocks, sh_blocks, hi_blocks;
+    int R;
+    int rows;                      // sub-sweep block height (binary32): 2, 4 or 8
+    DevState* sts;
+    unsigned long long* partial;
+    unsigned long long* hist;      // R x kHistBins
+    const double* edges2;
+    double* msd;                   // R net squared displacements (tracking launches)
+};
+void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k, bool track);
+void launch_subsweep_f64_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k);
+void launch_shift_batch(const BatchCtx& c, int prec, const void* src, void* dst, const SweepDraw* draws, int j);
+void launch_hist_batch(const BatchCtx& c, int prec, const void* arena);
 void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw);
 void launch_hist_f32(const LaunchCtx& c, const void* cells);
 

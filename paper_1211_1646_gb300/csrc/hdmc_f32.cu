@@ -3,11 +3,41 @@
 
 namespace hdmc {
 void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k) {
-    k_subsweep_f32<<<subsweep_grid(c.g), dim3(32, 4), 0, c.stream>>>(c.g, reinterpret_cast<float*>(cells), draw, k,
+    k_subsweep_f32<4><<<subsweep_grid(c.g), dim3(32, 4), 0, c.stream>>>(c.g, reinterpret_cast<float*>(cells), draw, k,
                                                                      c.partial);
 }
 void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     launch_shift_t<float>(c, src, dst, draw);
 }
 void launch_hist_f32(const LaunchCtx& c, const void* cells) { launch_hist_t<float>(c, cells); }
+
+void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k, bool track) {
+    float* a = reinterpret_cast<float*>(arena);
+#define HDMC_SUB_BATCH(ROWS, TRACK)                                                                        \
+    k_subsweep_f32_batch<ROWS, TRACK><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(c.reps, c.sub_map, a, draws, \
+                                                                                      c.R, j, k, c.partial, c.msd)
+    if (c.rows == 2) { if (track) HDMC_SUB_BATCH(2, true); else HDMC_SUB_BATCH(2, false); }
+    else if (c.rows == 8) { if (track) HDMC_SUB_BATCH(8, true); else HDMC_SUB_BATCH(8, false); }
+    else { if (track) HDMC_SUB_BATCH(4, true); else HDMC_SUB_BATCH(4, false); }
+#undef HDMC_SUB_BATCH
+}
+
+void launch_shift_batch(const BatchCtx& c, int prec, const void* src, void* dst, const SweepDraw* draws, int j) {
+    if (prec == 1)
+        k_shift_batch<float><<<c.sh_blocks, dim3(kShiftBX, kShiftBY), 0, c.stream>>>(
+            c.reps, c.sh_map, reinterpret_cast<const float*>(src), reinterpret_cast<float*>(dst), draws, c.R, j, c.sts);
+    else
+        k_shift_batch<double><<<c.sh_blocks, dim3(kShiftBX, kShiftBY), 0, c.stream>>>(
+            c.reps, c.sh_map, reinterpret_cast<const double*>(src), reinterpret_cast<double*>(dst), draws, c.R, j,
+            c.sts);
+}
+
+void launch_hist_batch(const BatchCtx& c, int prec, const void* arena) {
+    if (prec == 1)
+        k_hist_batch<float><<<c.hi_blocks, dim3(kHistBX, kHistBY), 0, c.stream>>>(
+            c.reps, c.hi_map, reinterpret_cast<const float*>(arena), c.edges2, c.hist);
+    else
+        k_hist_batch<double><<<c.hi_blocks, dim3(kHistBX, kHistBY), 0, c.stream>>>(
+            c.reps, c.hi_map, reinterpret_cast<const double*>(arena), c.edges2, c.hist);
+}
 }  // namespace hdmc

@@ -157,10 +157,13 @@ __device__ __forceinline__ float approx_f32(double v) {
     return e < 897u ? __uint_as_float(hi & 0x80000000u) : __uint_as_float(f);
 }
 
-// per-block trial counters: partial[4b + {trials, accepted, left, overlap}]
+// Per-block trial counters: bpart[{trials, accepted, left, overlap}] of this
+// block's own slot (blocks with the same slot run in stream order, so the
+// read-modify-write needs no atomics).
+template <int ROWS>
 __device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned int n_acc, unsigned int n_leave,
-                                                   unsigned long long* __restrict__ partial) {
-    __shared__ unsigned int red[4][3];
+                                                   unsigned long long* __restrict__ bpart) {
+    __shared__ unsigned int red[ROWS][3];
     const unsigned a = __reduce_add_sync(0xffffffffu, n_tr);
     const unsigned b = __reduce_add_sync(0xffffffffu, n_acc);
     const unsigned c = __reduce_add_sync(0xffffffffu, n_leave);
@@ -171,14 +174,17 @@ __device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned i
     }
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const unsigned tr = red[0][0] + red[1][0] + red[2][0] + red[3][0];
-        const unsigned ac = red[0][1] + red[1][1] + red[2][1] + red[3][1];
-        const unsigned lv = red[0][2] + red[1][2] + red[2][2] + red[3][2];
-        unsigned long long* p = partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x);
-        p[0] += tr;
-        p[1] += ac;
-        p[2] += lv;
-        p[3] += tr - ac - lv;
+        unsigned tr = 0, ac = 0, lv = 0;
+#pragma unroll
+        for (int w = 0; w < ROWS; ++w) {
+            tr += red[w][0];
+            ac += red[w][1];
+            lv += red[w][2];
+        }
+        bpart[0] += tr;
+        bpart[1] += ac;
+        bpart[2] += lv;
+        bpart[3] += tr - ac - lv;
     }
 }
 
@@ -226,15 +232,21 @@ __device__ __forceinline__ int dir_dy(int c) { return c < 3 ? -1 : (c < 5 ? 0 : 
 // cell's frame, is held in registers as packed binary32 pairs; their slot
 // pair (2,3) is read (from L1) and tested only in directions where some lane
 // of the warp has a third disk.
-static __global__ void __launch_bounds__(128, 5)
-k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
-               unsigned long long* __restrict__ partial) {
-    __shared__ float2 sdir[kDirChunk][128];
+// Block (bx, by) of the launch covers set columns 32 bx .. 32 bx + 31 and set
+// rows ROWS by .. ROWS by + ROWS - 1 (thread (x, y) of a 32 x ROWS block).
+// With TRACK, the block also adds the net squared displacement of its disks
+// over the cell update (final minus start position, summed over the disks)
+// to *msd: a sampling-efficiency measure used by the batch autotuner.
+template <int ROWS, bool TRACK = false>
+__device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restrict__ cells,
+                                             const SweepDraw* __restrict__ draw, int k, int bx, int by,
+                                             unsigned long long* __restrict__ bpart,
+                                             float2 (*__restrict__ sdir)[32 * ROWS], double* msd = nullptr) {
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int Q = draw->perm[k];
     const uint32_t sweep = draw->sweep;
-    const int hx = blockIdx.x * 32 + threadIdx.x;
-    const int hy = blockIdx.y * 4 + threadIdx.y;
+    const int hx = bx * 32 + threadIdx.x;
+    const int hy = by * ROWS + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
     const Neighbourhood nbh(g, Q, hx, hy);
@@ -271,6 +283,7 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
     const bool own23 = __any_sync(0xffffffffu, n >= 3);
 
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
+    float net2 = 0.f;
     if (n > 0) {
         uint32_t blk = 0;
         // shuffle (Alg. 1 line 5): one draw in [0, n!) by 21-bit Lemire on field 0
@@ -286,6 +299,14 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
             const uint32_t pk = perm_from_index(n, kk);
             permute(own.x, pk);
             permute(own.y, pk);
+        }
+        float sx0[4], sy0[4];
+        if (TRACK) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                sx0[j] = own.x[j];
+                sy0[j] = own.y[j];
+            }
         }
         // neighbour slots 0,1 translated into this cell's frame
         f2x qx01[8], qy01[8];
@@ -372,8 +393,29 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
         }
         n_tr = (unsigned)g.nsel;
         store_cell(ownp, own);
+        if (TRACK) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ex = own.x[j] - sx0[j], ey = own.y[j] - sy0[j];
+                net2 += ex * ex + ey * ey;
+            }
+        }
     }
-    add_block_counters(n_tr, n_acc, n_leave, partial);
+    if (TRACK) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) net2 += __shfl_xor_sync(0xffffffffu, net2, o);
+        if (threadIdx.x == 0) atomicAdd(msd, (double)net2);
+    }
+    add_block_counters<ROWS>(n_tr, n_acc, n_leave, bpart);
+}
+
+template <int ROWS>
+static __global__ void __launch_bounds__(32 * ROWS, 20 / ROWS)
+k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
+               unsigned long long* __restrict__ partial) {
+    __shared__ float2 sdir[kDirChunk][32 * ROWS];
+    subsweep_f32<ROWS>(g, cells, draw, k, blockIdx.x, blockIdx.y,
+                       partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
 }
 
 // ---- binary64 sub-sweep ---------------------------------------------------------------
@@ -423,13 +465,13 @@ __device__ __forceinline__ long long sym52_int(uint32_t hi, uint32_t lo) {
 }
 __device__ __forceinline__ float sym52_est(long long m) { return (float)(int)(m >> 29) * 0x1p-23f; }
 
-static __global__ void __launch_bounds__(128, 3)
-k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
-               unsigned long long* __restrict__ partial) {
+__device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restrict__ cells,
+                                             const SweepDraw* __restrict__ draw, int k, int bx, int by,
+                                             unsigned long long* __restrict__ bpart) {
     const int Q = draw->perm[k];
     const uint32_t sweep = draw->sweep;
-    const int hx = blockIdx.x * 32 + threadIdx.x;
-    const int hy = blockIdx.y * 4 + threadIdx.y;
+    const int hx = bx * 32 + threadIdx.x;
+    const int hy = by * 4 + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
     const Neighbourhood nbh(g, Q, hx, hy);
@@ -570,7 +612,14 @@ k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __
         }
         store_cell(ownp, own);
     }
-    add_block_counters(n_tr, n_acc, n_leave, partial);
+    add_block_counters<4>(n_tr, n_acc, n_leave, bpart);
+}
+
+static __global__ void __launch_bounds__(128, 3)
+k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
+               unsigned long long* __restrict__ partial) {
+    subsweep_f64(g, cells, draw, k, blockIdx.x, blockIdx.y,
+                 partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 // ---- cell shift: Alg. 4 ----------------------------------------------------------------
@@ -601,12 +650,11 @@ template <> struct Prm<double> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const SweepDraw* __restrict__ draw,
-        DevState* __restrict__ st) {
-    const int hx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int hy = blockIdx.y * blockDim.y + threadIdx.y;
-    const int q = blockIdx.z;
+__device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restrict__ src, T* __restrict__ dst,
+                                            const SweepDraw* __restrict__ draw, DevState* __restrict__ st, int bx,
+                                            int by, int q) {
+    const int hx = bx * kShiftBX + threadIdx.x;
+    const int hy = by * kShiftBY + threadIdx.y;
     const int fdir = draw->fdir;
     const int ax = fdir >> 1;
     const int sgn = (fdir & 1) ? -1 : 1;
@@ -662,6 +710,13 @@ k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const 
     store_cell(dst + 8 * idx, r);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kShiftBX * kShiftBY)
+k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const SweepDraw* __restrict__ draw,
+        DevState* __restrict__ st) {
+    shift_cells<T>(g, src, dst, draw, st, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // ---- contact histogram: Sec. 4 ------------------------------------------------------
 // Ordered pairs (i, j != i) at distance r in [sigma, sigma + 200 dr), in bins
 // [sigma + b dr, sigma + (b+1) dr) decided on the binary64 r^2 against the
@@ -674,18 +729,17 @@ __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return approx_f32(v); }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_hist(const Geometry g, const T* __restrict__ cells, const double* __restrict__ edges2,
-       unsigned long long* __restrict__ hist) {
+__device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restrict__ cells,
+                                           const double* __restrict__ edges2, unsigned long long* __restrict__ hist,
+                                           int bx, int by, int q) {
     __shared__ unsigned int sh[kHistBins];
     __shared__ double sE[kHistBins + 1];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y) sh[b] = 0u;
     for (int b = tid; b <= kHistBins; b += blockDim.x * blockDim.y) sE[b] = edges2[b];
     __syncthreads();
-    const int hx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int hy = blockIdx.y * blockDim.y + threadIdx.y;
-    const int q = blockIdx.z;
+    const int hx = bx * kHistBX + threadIdx.x;
+    const int hy = by * kHistBY + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     Cell<T> own;
 #pragma unroll
@@ -764,6 +818,73 @@ k_hist(const Geometry g, const T* __restrict__ cells, const double* __restrict__
         if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kHistBX * kHistBY)
+k_hist(const Geometry g, const T* __restrict__ cells, const double* __restrict__ edges2,
+       unsigned long long* __restrict__ hist) {
+    hist_cells<T>(g, cells, edges2, hist, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---- batched replicas ------------------------------------------------------------------
+// Every stage is one launch over all replicas of a batch: the launch's flat
+// block index is mapped to (replica, local block) by a per-stage table, and
+// each replica keeps its own geometry, cells, draws, device state,
+// counters and histogram.  Replica r's cells start at cell rd.cell_off of
+// the arena; its sweep draws of chunk position j sit at draws[j*R + r].
+template <int ROWS, bool TRACK>
+static __global__ void __launch_bounds__(32 * ROWS, 20 / ROWS)
+k_subsweep_f32_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __restrict__ map,
+                     float* __restrict__ arena, const SweepDraw* __restrict__ draws, int R, int j, int k,
+                     unsigned long long* __restrict__ partial, double* __restrict__ msd) {
+    __shared__ float2 sdir[kDirChunk][32 * ROWS];
+    const int r = map[blockIdx.x];
+    const ReplicaDesc* rd = reps + r;
+    const int local = (int)blockIdx.x - rd->sub_block0;
+    const int by = local / rd->sub_gx, bx = local - by * rd->sub_gx;
+    subsweep_f32<ROWS, TRACK>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
+                              partial + 4 * (rd->part_off + local), sdir, msd + r);
+}
+
+static __global__ void __launch_bounds__(128, 3)
+k_subsweep_f64_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __restrict__ map,
+                     double* __restrict__ arena, const SweepDraw* __restrict__ draws, int R, int j, int k,
+                     unsigned long long* __restrict__ partial) {
+    const int r = map[blockIdx.x];
+    const ReplicaDesc* rd = reps + r;
+    const int local = (int)blockIdx.x - rd->sub_block0;
+    const int by = local / rd->sub_gx, bx = local - by * rd->sub_gx;
+    subsweep_f64(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
+                 partial + 4 * (rd->part_off + local));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kShiftBX * kShiftBY)
+k_shift_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __restrict__ map,
+              const T* __restrict__ src, T* __restrict__ dst, const SweepDraw* __restrict__ draws, int R, int j,
+              DevState* __restrict__ sts) {
+    const int r = map[blockIdx.x];
+    const ReplicaDesc* rd = reps + r;
+    const int local = (int)blockIdx.x - rd->sh_block0;
+    const int per_set = rd->sh_gx * rd->sh_gy;
+    const int q = local / per_set, rem = local - q * per_set;
+    const int by = rem / rd->sh_gx, bx = rem - by * rd->sh_gx;
+    shift_cells<T>(rd->g, src + 8 * rd->cell_off, dst + 8 * rd->cell_off, draws + (size_t)j * R + r, sts + r, bx,
+                   by, q);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHistBX * kHistBY)
+k_hist_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __restrict__ map,
+             const T* __restrict__ arena, const double* __restrict__ edges2, unsigned long long* __restrict__ hist) {
+    const int r = map[blockIdx.x];
+    const ReplicaDesc* rd = reps + r;
+    const int local = (int)blockIdx.x - rd->hi_block0;
+    const int per_set = rd->hi_gx * rd->hi_gy;
+    const int q = local / per_set, rem = local - q * per_set;
+    const int by = rem / rd->hi_gx, bx = rem - by * rd->hi_gx;
+    hist_cells<T>(rd->g, arena + 8 * rd->cell_off, edges2, hist + (size_t)r * kHistBins, bx, by, q);
+}
+
 // ---- launchers ---------------------------------------------------------------------
 inline dim3 set_grid(const Geometry& g, dim3 block) {
     return dim3((unsigned)((g.hx + block.x - 1) / block.x), (unsigned)((g.hy + block.y - 1) / block.y), 4u);
@@ -771,14 +892,14 @@ inline dim3 set_grid(const Geometry& g, dim3 block) {
 
 template <typename T>
 void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
-    const dim3 block(64, 4);
+    const dim3 block(kShiftBX, kShiftBY);
     k_shift<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(src),
                                                                reinterpret_cast<T*>(dst), draw, c.st);
 }
 
 template <typename T>
 void launch_hist_t(const LaunchCtx& c, const void* cells) {
-    const dim3 block(32, 8);
+    const dim3 block(kHistBX, kHistBY);
     k_hist<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), c.edges2,
                                                               c.hist);
 }

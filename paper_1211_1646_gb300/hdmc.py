@@ -52,6 +52,21 @@ SIGNATURES = {
     "hdmc_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p, _f64p]),
     "hdmc_histogram_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_double, _u64p, _vp]),
+    "hdmc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, _i64p, _f64p, _f64p, ctypes.c_double,
+                                                     ctypes.c_int]),
+    "hdmc_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, _f64p, _f64p, ctypes.c_double,
+                                         _f64p, _i32p, _u64p, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "hdmc_batch_sweep": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "hdmc_batch_sample": (ctypes.c_int, [_vp]),
+    "hdmc_batch_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
+    "hdmc_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _u8p]),
+    "hdmc_batch_counters": (ctypes.c_int, [_vp, _u64p]),
+    "hdmc_batch_info": (ctypes.c_int, [_vp, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _u64p, _f64p]),
+    "hdmc_batch_set_nselect": (ctypes.c_int, [_vp, _i32p]),
+    "hdmc_batch_set_rows": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "hdmc_batch_config": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "hdmc_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, _i32p]),
+    "hdmc_batch_destroy": (None, [_vp]),
     "hdmc_destroy": (None, [_vp]),
     "hdmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -219,7 +234,98 @@ def hdmc_destroy(h):
         lib().hdmc_destroy(h)
 
 
-# ---- convenience wrapper ---------------------------------------------------------
+def _arr(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def hdmc_batch_workspace_bytes(N, Lx, Ly, sigma, precision):
+    N, Lx, Ly = _arr(N, np.int64), _arr(Lx, np.float64), _arr(Ly, np.float64)
+    return int(lib().hdmc_batch_workspace_bytes(len(N), _p(N, _i64p), _p(Lx, _f64p), _p(Ly, _f64p), sigma,
+                                                _precision(precision)))
+
+
+def hdmc_batch_create(N, Lx, Ly, sigma, d, nselect, seeds, precision, dev_workspace=None, workspace_bytes=0,
+                      stream=None):
+    N, Lx, Ly, d = _arr(N, np.int64), _arr(Lx, np.float64), _arr(Ly, np.float64), _arr(d, np.float64)
+    ns = None if nselect is None else _arr(nselect, np.int32)
+    sd = _arr([s & 0xFFFFFFFFFFFFFFFF for s in seeds], np.uint64)
+    b = _vp()
+    _check(lib().hdmc_batch_create(ctypes.byref(b), len(N), _p(N, _i64p), _p(Lx, _f64p), _p(Ly, _f64p), sigma,
+                                   _p(d, _f64p), None if ns is None else _p(ns, _i32p), _p(sd, _u64p),
+                                   _precision(precision), dev_workspace, workspace_bytes, stream), "hdmc_batch_create")
+    return b
+
+
+def hdmc_batch_sweep(b, n):
+    _check(lib().hdmc_batch_sweep(b, n), "hdmc_batch_sweep")
+
+
+def hdmc_batch_sample(b):
+    _check(lib().hdmc_batch_sample(b), "hdmc_batch_sample")
+
+
+def hdmc_batch_pressure(b, R):
+    """Returns (betaP_over_rho[R], g_contact[R], hist[R, 200], n_samples)."""
+    bp, g0 = np.zeros(R), np.zeros(R)
+    hist = np.zeros(R * HDMC_HIST_BINS, dtype=np.uint64)
+    ns = ctypes.c_int64()
+    _check(lib().hdmc_batch_pressure(b, _p(bp, _f64p), _p(g0, _f64p), _p(hist, _u64p), ctypes.byref(ns)),
+           "hdmc_batch_pressure")
+    return bp, g0, hist.reshape(R, HDMC_HIST_BINS), ns.value
+
+
+def hdmc_batch_get_state(b, r, C):
+    loc = np.zeros(8 * C, dtype=np.float64)
+    cnt = np.zeros(C, dtype=np.uint8)
+    _check(lib().hdmc_batch_get_state(b, r, _p(loc, _f64p), _p(cnt, _u8p)), "hdmc_batch_get_state")
+    return loc.reshape(C, 4, 2), cnt
+
+
+def hdmc_batch_counters(b, R):
+    out = np.zeros(4 * R, dtype=np.uint64)
+    _check(lib().hdmc_batch_counters(b, _p(out, _u64p)), "hdmc_batch_counters")
+    return out.reshape(R, 4)
+
+
+def hdmc_batch_info(b, r):
+    mx, my = ctypes.c_int32(), ctypes.c_int32()
+    wx, wy = ctypes.c_double(), ctypes.c_double()
+    sw = ctypes.c_uint64()
+    org = np.zeros(2, dtype=np.float64)
+    _check(lib().hdmc_batch_info(b, r, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(wx), ctypes.byref(wy),
+                                 ctypes.byref(sw), _p(org, _f64p)), "hdmc_batch_info")
+    return {"mx": mx.value, "my": my.value, "wx": wx.value, "wy": wy.value, "sweeps_done": sw.value,
+            "origin": org}
+
+
+def hdmc_batch_set_nselect(b, nselect):
+    ns = _arr(nselect, np.int32)
+    _check(lib().hdmc_batch_set_nselect(b, _p(ns, _i32p)), "hdmc_batch_set_nselect")
+
+
+def hdmc_batch_set_rows(b, rows):
+    _check(lib().hdmc_batch_set_rows(b, rows), "hdmc_batch_set_rows")
+
+
+def hdmc_batch_config(b, R):
+    rows = ctypes.c_int32()
+    ns = np.zeros(R, dtype=np.int32)
+    _check(lib().hdmc_batch_config(b, ctypes.byref(rows), _p(ns, _i32p)), "hdmc_batch_config")
+    return rows.value, ns
+
+
+def hdmc_batch_autotune(b, sweeps):
+    rows, nm = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().hdmc_batch_autotune(b, sweeps, ctypes.byref(rows), ctypes.byref(nm)), "hdmc_batch_autotune")
+    return rows.value, nm.value
+
+
+def hdmc_batch_destroy(b):
+    if b is not None and b.value:
+        lib().hdmc_batch_destroy(b)
+
+
+# ---- convenience wrappers ----------------------------------------------------------
 
 class System:
     """One hard-disk system on the current CUDA device.
@@ -305,3 +411,74 @@ class System:
         if self.precision == HDMC_FP64:
             return self.Lx, self.Ly
         return self.mx * float(np.float32(self.wx)), self.my * float(np.float32(self.wy))
+
+
+class Batch:
+    """R independent systems advanced together (one launch per stage for all).
+
+    replicas: list of objects with N, Lx, Ly, d, nselect, seed attributes
+    (e.g. workloads.Workload).  Workspace and stream from PyTorch as in System.
+    """
+
+    def __init__(self, replicas, sigma=1.0, precision="fp32", stream=None, device=None):
+        import torch
+
+        self.R = len(replicas)
+        self.N = [int(w.N) for w in replicas]
+        self.precision = _precision(precision)
+        Lx = [w.Lx for w in replicas]
+        Ly = [w.Ly for w in replicas]
+        nbytes = hdmc_batch_workspace_bytes(self.N, Lx, Ly, sigma, self.precision)
+        if nbytes == 0:
+            raise HDMCError(HDMC_EINVAL, "hdmc_batch_workspace_bytes")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        self.b = None
+        self.b = hdmc_batch_create(self.N, Lx, Ly, sigma, [w.d for w in replicas], [w.nselect for w in replicas],
+                                   [w.seed for w in replicas], self.precision, ptr, nbytes, stream)
+        self.grids = [hdmc_batch_info(self.b, r) for r in range(self.R)]
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            hdmc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        hdmc_batch_sweep(self.b, n)
+
+    def sample(self):
+        hdmc_batch_sample(self.b)
+
+    def pressure(self):
+        return hdmc_batch_pressure(self.b, self.R)
+
+    def state(self, r):
+        g = self.grids[r]
+        return hdmc_batch_get_state(self.b, r, g["mx"] * g["my"])
+
+    def counters(self):
+        return hdmc_batch_counters(self.b, self.R)
+
+    def origin(self, r):
+        return hdmc_batch_info(self.b, r)["origin"]
+
+    def set_rows(self, rows):
+        hdmc_batch_set_rows(self.b, rows)
+
+    def set_nselect(self, nselect):
+        hdmc_batch_set_nselect(self.b, nselect)
+
+    def config(self):
+        return hdmc_batch_config(self.b, self.R)
+
+    def autotune(self, sweeps=32):
+        return hdmc_batch_autotune(self.b, sweeps)

@@ -1,0 +1,136 @@
+"""Batched replicas through the C ABI.
+
+A replica of a batch is, by construction, the system hdmc_create builds from
+the same arguments: its trajectory must be bit-identical to the single-system
+run (and so to the oracle), whatever the block layout of the batched launches.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import pressure as P
+from paper_1211_1646_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _replicas():
+    Lx1, Ly1 = W.square_box(1024, 0.70)
+    nx, ny = W.hex_counts(2048)
+    Lx3, Ly3 = W.hex_box(nx, ny, 0.65)
+    Lx4, Ly4 = W.hex_box(64, 64, 0.72)
+    return [
+        W.Workload("a", 1024, Lx1, Ly1, 0.15, 4, 11, 0),
+        W.Workload("b", 600, 37.3, 23.9, 0.2, 7, 12, 0),        # ragged 36 x 22 grid
+        W.Workload("c", nx * ny, Lx3, Ly3, 0.1, 2, 13, 0),
+        W.Workload("d", 4096, Lx4, Ly4, 0.08, 1, 14, 0),
+    ]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1211_1646_gb300 import build
+    build.build()
+
+
+def _singles(reps, prec):
+    from paper_1211_1646_gb300 import hdmc
+    return [hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, w.seed, prec) for w in reps]
+
+
+def _same_as_singles(b, singles):
+    cnt_b = b.counters()
+    for r, s in enumerate(singles):
+        lb, cb = b.state(r)
+        ls, cs = s.state()
+        assert np.array_equal(cb, cs), "replica %d counts" % r
+        assert np.array_equal(lb, ls), "replica %d positions" % r
+        assert np.array_equal(cnt_b[r], s.counters()), "replica %d counters" % r
+        assert np.array_equal(b.origin(r), s.origin()), "replica %d origin" % r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_equals_single_systems(prec):
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision=prec)
+    singles = _singles(reps, prec)
+    b.sweep(70)                      # one 64-sweep graph plus a 6-sweep graph
+    for s in singles:
+        s.sweep(70)
+    _same_as_singles(b, singles)
+
+
+def test_batch_block_layout_does_not_change_results():
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision="fp32")
+    singles = _singles(reps, "fp32")
+    for rows in (2, 8, 4, 2):
+        b.set_rows(rows)
+        b.sweep(9)
+        for s in singles:
+            s.sweep(9)
+        _same_as_singles(b, singles)
+    assert b.config()[0] == 2
+
+
+def test_batch_matches_oracle_and_pressure():
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision="fp32")
+    orcs = [O.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, w.seed, O.FP32) for w in reps]
+    b.sweep(12)
+    b.sample()
+    for o in orcs:
+        o.sweep(12)
+    bp, g0, hist, ns = b.pressure()
+    assert ns == 1
+    for r, (w, o) in enumerate(zip(reps, orcs)):
+        assert np.array_equal(b.state(r)[0], o.state()[0])
+        h = o.histogram()
+        assert np.array_equal(hist[r], h)
+        bp_ref, _, _ = P.pressure(h, 1, w.N, w.Lx * w.Ly)
+        assert abs(bp[r] - bp_ref) < 1e-9 * abs(bp_ref)
+
+
+def test_batch_autotune_and_invariants():
+    from scipy.spatial import cKDTree
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision="fp32")
+    rows, nm = b.autotune(16)
+    assert rows in (2, 4, 8) and nm in (1, 2, 4, 8)
+    assert b.config()[0] == rows and list(b.config()[1]) == [nm] * len(reps)
+    b.sweep(40)
+    cnt = b.counters()
+    for r, w in enumerate(reps):
+        loc, c = b.state(r)
+        assert int(c.sum()) == w.N and c.max() <= 4
+        assert cnt[r, 0] == cnt[r, 1] + cnt[r, 2] + cnt[r, 3]
+        g = b.grids[r]
+        wx, wy = float(np.float32(g["wx"])), float(np.float32(g["wy"]))
+        occ = np.arange(4)[None, :] < c[:, None]
+        cx = np.repeat(np.arange(g["mx"] * g["my"]) % g["mx"], 4).reshape(-1, 4)
+        cy = np.repeat(np.arange(g["mx"] * g["my"]) // g["mx"], 4).reshape(-1, 4)
+        X = (cx * wx + loc[..., 0])[occ]
+        Y = (cy * wy + loc[..., 1])[occ]
+        org = b.origin(r)
+        box = np.array([g["mx"] * wx, g["my"] * wy])
+        xy = np.mod(np.stack([X + org[0], Y + org[1]], 1), box)
+        assert len(cKDTree(xy, boxsize=box).query_pairs(1.0 - 1e-6)) == 0
+
+
+def test_batch_of_64_replicas_runs():
+    from paper_1211_1646_gb300 import hdmc
+    reps = W.batch64()
+    b = hdmc.Batch(reps, precision="fp32")
+    b.sweep(5)
+    b.sample()
+    bp, g0, hist, ns = b.pressure()
+    assert np.all(np.isfinite(bp)) and np.all(bp > 1.0)
+    cnt = b.counters()
+    assert np.all(cnt[:, 0] > 0)
