@@ -223,25 +223,52 @@ __device__ __forceinline__ int dir_dx(int c) { return (c == 1 || c == 6) ? 0 : (
 __device__ __forceinline__ int dir_dy(int c) { return c < 3 ? -1 : (c < 5 ? 0 : 1); }
 
 // ---- binary32 sub-sweep: Alg. 1 lines 4-13 / Alg. 2 ----------------------------------
-// One thread per active cell of set Q = draw->perm[k]; block 32 x 4 over the
-// set's half-resolution grid.  The thread draws its cell's shuffle and trial
-// directions from the cell's stream (kept directions staged in shared
-// memory), shuffles its disks, then makes n_M trial moves visiting the slots
-// cyclically.  The 8 neighbouring cells belong to other sets and are not
-// written by this launch.  Their slot pair (0,1), translated into this
-// cell's frame, is held in registers as packed binary32 pairs; their slot
-// pair (2,3) is read (from L1) and tested only in directions where some lane
-// of the warp has a third disk.
-// Block (bx, by) of the launch covers set columns 32 bx .. 32 bx + 31 and set
-// rows ROWS by .. ROWS by + ROWS - 1 (thread (x, y) of a 32 x ROWS block).
+// One thread per active cell of set Q = draw->perm[k]; block 32 x ROWS over
+// the set's half-resolution grid.  Phases, ordered so that the latency of the
+// cell loads is covered by work that does not need them:
+//   1. issue the loads of the own cell and of the 8 neighbouring cells (they
+//      belong to other sets and are not written by this launch);
+//   2. draw the trial directions of the cell's stream (kept attempts staged
+//      in shared memory, kDirChunk at a time);
+//   3. shuffle the disks with the draw in field 0 of the stream's first block,
+//      translate neighbour slot pair (0,1) into this cell's frame as packed
+//      binary32 pairs, flag (warp-uniformly) the directions where some lane
+//      has a third disk;
+//   4. n_M trial moves, visiting the shuffled slots cyclically.
+// NSEL > 0 fixes n_M at compile time (the trial loop is then unrolled).
 // With TRACK, the block also adds the net squared displacement of its disks
 // over the cell update (final minus start position, summed over the disks)
 // to *msd: a sampling-efficiency measure used by the batch autotuner.
-template <int ROWS, bool TRACK = false>
+template <int ROWS>
+__device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t sweep, uint32_t cell, uint32_t c2,
+                                                uint32_t F[6], uint32_t& blk, int& pnext, int want,
+                                                float2 (*__restrict__ sdir)[32 * ROWS], int tid) {
+    int have = 0;
+    for (;;) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            if (p >= pnext && have < want) {
+                const float u = sym21(F[2 * p]), v = sym21(F[2 * p + 1]);
+                if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) {
+                    sdir[have][tid] = make_float2(u, v);
+                    ++have;
+                }
+                pnext = p + 1;
+            }
+        }
+        if (have >= want) break;
+        ++blk;
+        fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+        pnext = 0;
+    }
+}
+
+template <int ROWS, int NSEL, bool TRACK = false>
 __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restrict__ cells,
                                              const SweepDraw* __restrict__ draw, int k, int bx, int by,
                                              unsigned long long* __restrict__ bpart,
                                              float2 (*__restrict__ sdir)[32 * ROWS], double* msd = nullptr) {
+    const int nsel = NSEL > 0 ? NSEL : g.nsel;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int Q = draw->perm[k];
     const uint32_t sweep = draw->sweep;
@@ -251,13 +278,13 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
     const Neighbourhood nbh(g, Q, hx, hy);
 
+    // 1. loads
     Cell<float> own;
 #pragma unroll
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = (float)kEmpty;
     float* ownp = cells + 8 * (nbh.base[0] + (long long)hy * g.hx + hx);
     if (live) load_cell(ownp, own);
-    // slots 0,1 of the neighbours; slot 2 only to know whether it is used
-    float4 n01[8];
+    float4 n01[8];   // slots 0,1 of the neighbours (x0 x1 y0 y1); slot 2 only to flag its use
     float n2[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -271,11 +298,18 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
             n2[c] = __ldg(p + 2);
         }
     }
-    // first block of the cell's trial stream (independent of the loads in flight)
+
+    // 2. directions of the first chunk (the cell's trial stream)
     const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
     const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
     uint32_t F[6];
     fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
+    const uint32_t f0 = F[0];   // shuffle draw
+    uint32_t blk = 0;
+    int pnext = 1;               // next attempt: field pair 1 of block 0 (fields 2,3)
+    draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);
+
+    // 3. cell contents
     const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
     uint32_t dir23 = 0;   // warp-uniform: directions where some lane has a third disk
 #pragma unroll
@@ -285,11 +319,10 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
     float net2 = 0.f;
     if (n > 0) {
-        uint32_t blk = 0;
         // shuffle (Alg. 1 line 5): one draw in [0, n!) by 21-bit Lemire on field 0
         if (n >= 2) {
             const uint32_t range = factorial(n);
-            const uint32_t m = F[0] * range;
+            const uint32_t m = f0 * range;
             const uint32_t thr = n == 4 ? 8u : (n == 3 ? 2u : 0u);   // 2^21 mod n!
             uint32_t kk = m >> 21;
             if ((m & 0x1FFFFFu) < thr) {   // rejected: draw from the shuffle stream instead
@@ -308,7 +341,6 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 sy0[j] = own.y[j];
             }
         }
-        // neighbour slots 0,1 translated into this cell's frame
         f2x qx01[8], qy01[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -330,29 +362,13 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
         }
         const float df = g.df;
         const f2x ns2 = pk(-g.sig2f, -g.sig2f);
-        int pnext = 1;   // next attempt: field pair 1 of block 0 (fields 2,3)
+
+        // 4. trials
         int i = 0;
-        for (int t0 = 0; t0 < g.nsel; t0 += kDirChunk) {
-            const int want = min(kDirChunk, g.nsel - t0);
-            // directions: attempts (u,v) from consecutive field pairs, kept inside the unit disk
-            int have = 0;
-            for (;;) {
-#pragma unroll
-                for (int p = 0; p < 3; ++p) {
-                    if (p >= pnext && have < want) {
-                        const float u = sym21(F[2 * p]), v = sym21(F[2 * p + 1]);
-                        if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) {
-                            sdir[have][tid] = make_float2(u, v);
-                            ++have;
-                        }
-                        pnext = p + 1;
-                    }
-                }
-                if (have >= want) break;
-                ++blk;
-                fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
-                pnext = 0;
-            }
+        for (int t0 = 0; t0 < nsel; t0 += kDirChunk) {
+            const int want = min(kDirChunk, nsel - t0);
+            if (t0 > 0) draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, want, sdir, tid);
+#pragma unroll(NSEL > 0 ? (NSEL < kDirChunk ? NSEL : kDirChunk) : 1)
             for (int tt = 0; tt < want; ++tt) {
                 const float2 uv = sdir[tt][tid];
                 const float tx = __fmaf_rn(df, uv.x, pick(own.x, i));
@@ -391,7 +407,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 i = (i + 1 == n) ? 0 : i + 1;
             }
         }
-        n_tr = (unsigned)g.nsel;
+        n_tr = (unsigned)nsel;
         store_cell(ownp, own);
         if (TRACK) {
 #pragma unroll
@@ -409,13 +425,13 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     add_block_counters<ROWS>(n_tr, n_acc, n_leave, bpart);
 }
 
-template <int ROWS>
+template <int ROWS, int NSEL>
 static __global__ void __launch_bounds__(32 * ROWS, 20 / ROWS)
 k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
     __shared__ float2 sdir[kDirChunk][32 * ROWS];
-    subsweep_f32<ROWS>(g, cells, draw, k, blockIdx.x, blockIdx.y,
-                       partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
+    subsweep_f32<ROWS, NSEL>(g, cells, draw, k, blockIdx.x, blockIdx.y,
+                             partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
 }
 
 // ---- binary64 sub-sweep ---------------------------------------------------------------
@@ -841,7 +857,7 @@ k_subsweep_f32_batch(const ReplicaDesc* __restrict__ reps, const unsigned short*
     const ReplicaDesc* rd = reps + r;
     const int local = (int)blockIdx.x - rd->sub_block0;
     const int by = local / rd->sub_gx, bx = local - by * rd->sub_gx;
-    subsweep_f32<ROWS, TRACK>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
+    subsweep_f32<ROWS, 0, TRACK>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
                               partial + 4 * (rd->part_off + local), sdir, msd + r);
 }
 
