@@ -234,7 +234,6 @@ def run_hdmc(args, rank, world, dist):
     # kernel-level times on the same stream (direct launches with CUDA events)
     ms_sub, ms_shift, ms_draw = hdmc.hdmc_profile_sweeps(s32.h, 20)
     hbm_peak, peak_kind = load_peaks()
-    C = s32.C
     # algorithmic bytes of one sub-sweep launch: every live particle read once
     # (the halos of the active cells cover the grid) + the active set's
     # particles written once: 1.25 * N * 8 B (binary32 offsets)
@@ -242,20 +241,22 @@ def run_hdmc(args, rank, world, dist):
     achieved = bytes_sub / (ms_sub / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers ----
-    loc, cnt = s32.state()
-    info = s32.info()
-    h2d = C * 4 * 8
-    d2h = C * 4 * 8 + 200 * 8
+    # Each step loads the system's snapshot from pinned host memory (H2D),
+    # runs the step (its histogram and pressure come back to the host) and
+    # writes the new snapshot back (D2H).
+    snap = torch.empty(s32.snapshot_bytes(), dtype=torch.uint8, pin_memory=True)
+    s32.save(snap)
+    h2d = snap.numel()
+    d2h = snap.numel() + 200 * 8
     e2e_trials, e2e_s = 0, 0.0
     torch.cuda.synchronize(dev)
     for k in range(max(1, args.steps)):
         c0 = int(s32.counters()[0])
         t0 = time.perf_counter()
-        s32.set_state(loc, cnt, info["origin"], info["sweeps_done"], info["shifts_done"])   # H2D
-        bp, g0, _, _ = one_step(s32)                                                       # D2H histogram
-        loc, cnt = s32.state()                                                              # D2H state
+        s32.load(snap)                        # H2D: the step's input state
+        bp, g0, _, _ = one_step(s32)          # D2H: histogram -> pressure
+        s32.save(snap)                        # D2H: the state after the step
         t1 = time.perf_counter()
-        info = s32.info()
         e2e_trials += int(s32.counters()[0]) - c0
         e2e_s += t1 - t0
     e2e_s = max_over_ranks(e2e_s)

@@ -141,6 +141,41 @@ int hdmc_get_state(hdmc_t *h, double *local, uint8_t *counts);
 int hdmc_set_state(hdmc_t *h, const double *local, const uint8_t *counts, const double origin[2],
                    uint64_t sweeps_done, uint64_t shifts_done);
 
+/* Snapshots (checkpoint / resume).  The paper does not describe saving a
+ * run; because every random draw is addressed by (seed, sweep, cell, set)
+ * counters (Sec. 3.2 draws a fresh stream per cell update), the image below
+ * determines the rest of the trajectory exactly.
+ *
+ * A snapshot is a byte image of the complete state of a system in the
+ * library's own device layout: a 256-byte header (magic "HDMCSNP1", format
+ * version, precision, N, box, sigma, move size d, n_M, seed, grid, sweep
+ * and shift counters, accumulated sample count), then, each at a 256-byte
+ * aligned offset, the device state word (grid origin, next sweep/shift
+ * index), the trial counters, the histogram accumulator and the cells
+ * (set-major, 4 slots per cell in the handle's coordinate type).  Images are
+ * portable between hosts of the same byte order.
+ *
+ * hdmc_snapshot_bytes returns the image size of this handle, or 0 for a
+ * NULL handle. */
+size_t hdmc_snapshot_bytes(const hdmc_t *h);
+
+/* Writes the snapshot of h into host buf (bytes >= hdmc_snapshot_bytes(h),
+ * else HDMC_EINVAL).  Pinned host memory makes the copy asynchronous to the
+ * host thread and fast; pageable memory also works.  Returns the device's
+ * pending error (HDMC_EOVERFLOW), if any, after writing the image.
+ * Synchronises. */
+int hdmc_save(hdmc_t *h, void *buf, size_t bytes);
+
+/* Restores a snapshot written by hdmc_save for a system of the same N, box,
+ * sigma and precision (d, n_M and seed are taken from the image).  The cells
+ * are copied to the device and checked there before anything is replaced:
+ * an image with a wrong header, an occupied slot after an empty one, a
+ * coordinate outside [0,w) (or NaN), an unused slot not holding
+ * HDMC_EMPTY_SLOT, or a disk total other than N is rejected with
+ * HDMC_EINVAL and the handle keeps its previous state.  Overlaps are not
+ * checked.  Synchronises. */
+int hdmc_load(hdmc_t *h, const void *buf, size_t bytes);
+
 /* Cumulative trial counters: out[0] trial moves attempted (n_M per occupied
  * active cell and sub-sweep), out[1] accepted, out[2] rejected because the
  * disk would leave its cell, out[3] rejected because of an overlap.

@@ -30,7 +30,7 @@ constexpr size_t kAlign = 256;   // workspace segment alignment
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t cells, table, shift_table, state, partial, hist, edges, total;
+    size_t cells, table, shift_table, state, partial, hist, edges, check, total;
     int nblocks;
 };
 
@@ -46,7 +46,8 @@ Layout make_layout(const Geometry& g, int prec) {
     L.partial = align_up(sizeof(unsigned long long) * 4 * (size_t)L.nblocks);
     L.hist = align_up(sizeof(unsigned long long) * kHistBins);
     L.edges = align_up(sizeof(double) * (kHistBins + 1));
-    L.total = 2 * L.cells + L.table + L.shift_table + L.state + L.partial + L.hist + L.edges;
+    L.check = align_up(2 * sizeof(unsigned long long));
+    L.total = 2 * L.cells + L.table + L.shift_table + L.state + L.partial + L.hist + L.edges + L.check;
     return L;
 }
 
@@ -71,6 +72,7 @@ struct hdmc_handle {
     unsigned long long* partial = nullptr;
     unsigned long long* hist = nullptr;
     double* edges2 = nullptr;
+    unsigned long long* check = nullptr;   // snapshot check: {disks, bad cell flag}
     uint64_t sweeps = 0, shifts = 0;
     int64_t n_samples = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (sweeps, parity) -> graph
@@ -241,6 +243,8 @@ int hdmc_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, dou
     h->hist = (unsigned long long*)p;
     p += h->lay.hist;
     h->edges2 = (double*)p;
+    p += h->lay.edges;
+    h->check = (unsigned long long*)p;
 
     e = cuda_code(cudaMemset(h->ws + 2 * h->lay.cells, 0, h->lay.total - 2 * h->lay.cells));
     if (!e) {
@@ -463,6 +467,159 @@ int hdmc_set_state(hdmc_t* h, const double* local, const uint8_t* counts, const 
     h->sweeps = sweeps_done;
     h->shifts = shifts_done;
     return e;
+}
+
+// ---- snapshots ------------------------------------------------------------------------
+namespace {
+
+constexpr char kSnapMagic[8] = {'H', 'D', 'M', 'C', 'S', 'N', 'P', '1'};
+constexpr uint32_t kSnapVersion = 1;
+constexpr size_t kSnapHeader = 256;
+
+struct SnapHeader {
+    char magic[8];
+    uint32_t version, precision;
+    int64_t N;
+    double Lx, Ly, sigma, d;
+    int32_t nsel, mx, my, nblocks;
+    uint32_t key0, key1;
+    uint64_t sweeps, shifts;
+    int64_t n_samples;
+    uint64_t off_state, off_partial, off_hist, off_cells, total;
+};
+static_assert(sizeof(SnapHeader) <= kSnapHeader, "snapshot header");
+
+struct SnapLayout {
+    size_t state, partial, hist, cells, cell_bytes, total;
+};
+
+SnapLayout snap_layout(const hdmc_t* h) {
+    SnapLayout L;
+    size_t p = kSnapHeader;
+    L.state = p;
+    p += align_up(sizeof(DevState));
+    L.partial = p;
+    p += align_up(sizeof(unsigned long long) * 4 * (size_t)h->lay.nblocks);
+    L.hist = p;
+    p += align_up(sizeof(unsigned long long) * kHistBins);
+    L.cells = p;
+    L.cell_bytes = (size_t)h->g.C * kSlots * (h->prec == HDMC_FP64 ? sizeof(double2) : sizeof(float2));
+    L.total = p + L.cell_bytes;
+    return L;
+}
+
+}  // namespace
+
+size_t hdmc_snapshot_bytes(const hdmc_t* h) { return h ? snap_layout(h).total : 0; }
+
+int hdmc_save(hdmc_t* h, void* buf, size_t bytes) {
+    if (!h || !buf) return HDMC_EINVAL;
+    const SnapLayout L = snap_layout(h);
+    if (bytes < L.total) return HDMC_EINVAL;
+    char* b = static_cast<char*>(buf);
+    SnapHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kSnapMagic, sizeof(kSnapMagic));
+    hd.version = kSnapVersion;
+    hd.precision = (uint32_t)h->prec;
+    hd.N = h->N;
+    hd.Lx = h->Lx;
+    hd.Ly = h->Ly;
+    hd.sigma = h->g.sigma;
+    hd.d = h->g.d;
+    hd.nsel = h->g.nsel;
+    hd.mx = h->g.mx;
+    hd.my = h->g.my;
+    hd.nblocks = h->lay.nblocks;
+    hd.key0 = h->g.key0;
+    hd.key1 = h->g.key1;
+    hd.sweeps = h->sweeps;
+    hd.shifts = h->shifts;
+    hd.n_samples = h->n_samples;
+    hd.off_state = L.state;
+    hd.off_partial = L.partial;
+    hd.off_hist = L.hist;
+    hd.off_cells = L.cells;
+    hd.total = L.total;
+    std::memset(b, 0, L.cells);
+    std::memcpy(b, &hd, sizeof(hd));
+    const cudaStream_t s = h->stream;
+    int e = cuda_code(cudaMemcpyAsync(b + L.state, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(b + L.partial, h->partial, sizeof(unsigned long long) * 4 * h->lay.nblocks,
+                                      cudaMemcpyDeviceToHost, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(b + L.hist, h->hist, sizeof(unsigned long long) * kHistBins,
+                                      cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaMemcpyAsync(b + L.cells, h->cells[h->cur], L.cell_bytes, cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    DevState ds;
+    std::memcpy(&ds, b + L.state, sizeof(ds));
+    return (ds.error & 1u) ? HDMC_EOVERFLOW : HDMC_OK;
+}
+
+int hdmc_load(hdmc_t* h, const void* buf, size_t bytes) {
+    if (!h || !buf) return HDMC_EINVAL;
+    const SnapLayout L = snap_layout(h);
+    if (bytes < L.total) return HDMC_EINVAL;
+    const char* b = static_cast<const char*>(buf);
+    SnapHeader hd;
+    std::memcpy(&hd, b, sizeof(hd));
+    const Geometry& g = h->g;
+    const bool same = std::memcmp(hd.magic, kSnapMagic, sizeof(kSnapMagic)) == 0 && hd.version == kSnapVersion &&
+                      hd.precision == (uint32_t)h->prec && hd.N == h->N && hd.Lx == h->Lx && hd.Ly == h->Ly &&
+                      hd.sigma == g.sigma && hd.mx == g.mx && hd.my == g.my && hd.nblocks == h->lay.nblocks &&
+                      hd.off_state == L.state && hd.off_partial == L.partial && hd.off_hist == L.hist &&
+                      hd.off_cells == L.cells && hd.total == L.total;
+    if (!same) return HDMC_EINVAL;
+    if (hd.nsel < 1 || hd.nsel > 255 || !(hd.d > 0) || !(hd.d < 0.5 * g.wx) || !(hd.d < 0.5 * g.wy) ||
+        hd.n_samples < 0)
+        return HDMC_EINVAL;
+    DevState ds;
+    std::memcpy(&ds, b + L.state, sizeof(ds));
+    if (ds.error != 0 || !std::isfinite(ds.origin[0]) || !std::isfinite(ds.origin[1])) return HDMC_EINVAL;
+
+    // cells: into the idle half of the double buffer, checked there
+    const cudaStream_t s = h->stream;
+    const LaunchCtx c = h->ctx(s);
+    void* idle = h->cells[h->cur ^ 1];
+    unsigned long long res[2] = {0, 0};
+    int e = cuda_code(cudaMemsetAsync(h->check, 0, 2 * sizeof(unsigned long long), s));
+    if (!e) e = cuda_code(cudaMemcpyAsync(idle, b + L.cells, L.cell_bytes, cudaMemcpyHostToDevice, s));
+    if (!e) {
+        if (h->prec == HDMC_FP64) launch_check_f64(c, idle, h->check);
+        else launch_check_f32(c, idle, h->check);
+        e = cuda_code(cudaGetLastError());
+    }
+    if (!e) e = cuda_code(cudaMemcpyAsync(res, h->check, sizeof(res), cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    if (res[1] != 0 || res[0] != (unsigned long long)h->N) return HDMC_EINVAL;
+
+    // commit
+    e = cuda_code(cudaMemcpyAsync(h->st, b + L.state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(h->partial, b + L.partial, sizeof(unsigned long long) * 4 * h->lay.nblocks,
+                                      cudaMemcpyHostToDevice, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(h->hist, b + L.hist, sizeof(unsigned long long) * kHistBins,
+                                      cudaMemcpyHostToDevice, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    h->cur ^= 1;
+    h->sweeps = hd.sweeps;
+    h->shifts = hd.shifts;
+    h->n_samples = hd.n_samples;
+    if (hd.d != g.d || hd.nsel != g.nsel || hd.key0 != g.key0 || hd.key1 != g.key1) {
+        h->g.d = hd.d;
+        h->g.df = (float)hd.d;
+        h->g.nsel = hd.nsel;
+        h->g.key0 = hd.key0;
+        h->g.key1 = hd.key1;
+        h->drop_graphs();   // recorded kernels carry the old parameters
+    }
+    return HDMC_OK;
 }
 
 int hdmc_counters(hdmc_t* h, uint64_t out[4]) {

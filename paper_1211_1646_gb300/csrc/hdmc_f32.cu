@@ -13,6 +13,9 @@ void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const Swee
     launch_shift_t<float>(c, src, dst, draw);
 }
 void launch_hist_f32(const LaunchCtx& c, const void* cells) { launch_hist_t<float>(c, cells); }
+void launch_check_f32(const LaunchCtx& c, const void* cells, unsigned long long* out) {
+    launch_check_t<float>(c, cells, out);
+}
 
 void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k, bool track) {
     float* a = reinterpret_cast<float*>(arena);

@@ -10,6 +10,9 @@ void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const Swee
     launch_shift_t<double>(c, src, dst, draw);
 }
 void launch_hist_f64(const LaunchCtx& c, const void* cells) { launch_hist_t<double>(c, cells); }
+void launch_check_f64(const LaunchCtx& c, const void* cells, unsigned long long* out) {
+    launch_check_t<double>(c, cells, out);
+}
 
 void launch_subsweep_f64_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k) {
     k_subsweep_f64_batch<<<c.sub_blocks, dim3(32, 4), 0, c.stream>>>(c.reps, c.sub_map, reinterpret_cast<double*>(arena),

@@ -920,4 +920,41 @@ void launch_hist_t(const LaunchCtx& c, const void* cells) {
                                                               c.hist);
 }
 
+// ---- snapshot check ---------------------------------------------------------------------
+// Checks every cell of an incoming image (any storage order): occupied slots
+// form a prefix, occupied coordinates lie in [0,wx) x [0,wy) of the
+// coordinate type, unused slots hold kEmpty in both coordinates.  out[0]
+// accumulates the number of disks, out[1] becomes non-zero on a bad cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_check_cells(const Geometry g, const T* __restrict__ cells,
+                                                     unsigned long long* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    unsigned n = 0;
+    bool bad = false;
+    if (i < g.C) {
+        Cell<T> c;
+        load_cell_ro(cells + 8 * i, c);
+        bool empty_seen = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (c.x[j] == T(kEmpty) && c.y[j] == T(kEmpty)) {
+                empty_seen = true;
+            } else {
+                bad |= empty_seen || !(c.x[j] >= T(0) && c.x[j] < Prm<T>::wx(g)) ||
+                       !(c.y[j] >= T(0) && c.y[j] < Prm<T>::wy(g));
+                ++n;
+            }
+        }
+    }
+    const unsigned tot = __reduce_add_sync(0xffffffffu, n);
+    if (threadIdx.x % 32 == 0 && tot) atomicAdd(out, (unsigned long long)tot);
+    if (bad) atomicOr(out + 1, 1ull);
+}
+
+template <typename T>
+void launch_check_t(const LaunchCtx& c, const void* cells, unsigned long long* out) {
+    const unsigned blocks = (unsigned)((c.g.C + 255) / 256);
+    k_check_cells<T><<<blocks, 256, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), out);
+}
+
 }  // namespace hdmc

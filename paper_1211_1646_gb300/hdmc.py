@@ -44,6 +44,9 @@ SIGNATURES = {
     "hdmc_positions": (ctypes.c_int, [_vp, _f64p, _i32p]),
     "hdmc_get_state": (ctypes.c_int, [_vp, _f64p, _u8p]),
     "hdmc_set_state": (ctypes.c_int, [_vp, _f64p, _u8p, _f64p, ctypes.c_uint64, ctypes.c_uint64]),
+    "hdmc_snapshot_bytes": (ctypes.c_size_t, [_vp]),
+    "hdmc_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "hdmc_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hdmc_counters": (ctypes.c_int, [_vp, _u64p]),
     "hdmc_info": (ctypes.c_int, [_vp, _i32p, _i32p, _f64p, _f64p, _u64p, _u64p, _f64p]),
     "hdmc_set_move_size": (ctypes.c_int, [_vp, ctypes.c_double]),
@@ -180,6 +183,33 @@ def hdmc_set_state(h, local, counts, origin, sweeps_done, shifts_done):
     org = np.ascontiguousarray(origin, dtype=np.float64)
     _check(lib().hdmc_set_state(h, _p(loc, _f64p), _p(cnt, _u8p), _p(org, _f64p), sweeps_done, shifts_done),
            "hdmc_set_state")
+
+
+def _host_buffer(buf):
+    """(address, size in bytes) of a contiguous host buffer: a numpy array or
+    a CPU torch tensor (pinned or not)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("snapshot buffer must be contiguous")
+        return buf.ctypes.data, buf.nbytes
+    if buf.device.type != "cpu" or not buf.is_contiguous():
+        raise ValueError("snapshot buffer must be a contiguous host tensor")
+    return buf.data_ptr(), buf.numel() * buf.element_size()
+
+
+def hdmc_snapshot_bytes(h):
+    return int(lib().hdmc_snapshot_bytes(h))
+
+
+def hdmc_save(h, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc_save(h, ptr, n), "hdmc_save")
+    return buf
+
+
+def hdmc_load(h, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc_load(h, ptr, n), "hdmc_load")
 
 
 def hdmc_counters(h):
@@ -394,6 +424,19 @@ class System:
 
     def counters(self):
         return hdmc_counters(self.h)
+
+    def snapshot_bytes(self):
+        return hdmc_snapshot_bytes(self.h)
+
+    def save(self, buf=None):
+        """Snapshot into buf (numpy uint8 array or host tensor, e.g. pinned);
+        a new numpy array when buf is None.  Returns the buffer."""
+        if buf is None:
+            buf = np.empty(self.snapshot_bytes(), dtype=np.uint8)
+        return hdmc_save(self.h, buf)
+
+    def load(self, buf):
+        hdmc_load(self.h, buf)
 
     def info(self):
         return hdmc_info(self.h)
