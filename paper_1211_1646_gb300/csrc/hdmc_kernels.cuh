@@ -738,25 +738,72 @@ k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const 
 // [sigma + b dr, sigma + (b+1) dr) decided on the binary64 r^2 against the
 // squared bin edges; distances from cell-local coordinates over the 5x5
 // neighbourhood (w >= sigma, so two rings reach past 1.02 sigma).  A binary32
-// estimate of r^2 with a wide margin selects the candidates; only those get
-// the binary64 distance.  One thread per cell,
-// grid (set row, set column, set); per-block shared histogram.
+// estimate of r^2 with a wide margin selects the candidates (about 0.7 per
+// disk); each warp queues its candidates in shared memory and computes the
+// binary64 distance and bin of 32 queued pairs at a time, so the (slow)
+// binary64 instructions run with every lane busy.  Non-negative doubles
+// order like their bit patterns read as signed integers, so the bin search
+// compares integers.  One thread per cell, grid (set row, set column, set);
+// per-block shared histogram.
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return approx_f32(v); }
+
+constexpr int kHistQueue = 64;   // per-warp candidate queue (< 32 pending + 32 appended)
+
+// Candidate entry: source lane (5 bits), own slot i (2), neighbour slot j (2),
+// dx + 2 (3), dy + 2 (3).
+__device__ __forceinline__ uint32_t hist_entry(int lane, int b, int dx, int dy) {
+    return (uint32_t)lane | ((uint32_t)(b >> 2) << 5) | ((uint32_t)(b & 3) << 7) | ((uint32_t)(dx + 2) << 9) |
+           ((uint32_t)(dy + 2) << 12);
+}
+
+// Bins the first `count` queued pairs, one per lane (warp-uniform call).
+template <typename T>
+__device__ __forceinline__ void hist_flush(const Geometry& g, const T* __restrict__ cells, const uint32_t* sq,
+                                           int count, int q, int bx, int hy, const long long* sEi,
+                                           unsigned int* sh, double wxd, double wyd, float sigf, float inv_drf) {
+    const int lane = threadIdx.x;
+    if (lane >= count) return;
+    const uint32_t e = sq[lane];
+    const int src = e & 31, i = (e >> 5) & 3, j = (e >> 7) & 3;
+    const int dx = (int)((e >> 9) & 7) - 2, dy = (int)((e >> 12) & 7) - 2;
+    const int hx = bx * kHistBX + src;
+    const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
+    const T* own = cells + 8 * ((long long)q * g.cq + (long long)hy * g.hx + hx);
+    const T* nb = cells + 8 * storage_index(g, wrap(cx + dx, g.mx), wrap(cy + dy, g.my));
+    const double px = (double)__ldg(own + i), py = (double)__ldg(own + 4 + i);
+    const double ex = __dadd_rn((double)__ldg(nb + j), (double)dx * wxd);
+    const double ey = __dadd_rn((double)__ldg(nb + 4 + j), (double)dy * wyd);
+    const double ddx = __dsub_rn(px, ex), ddy = __dsub_rn(py, ey);
+    const double r2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+    const long long r2i = __double_as_longlong(r2);   // r2 >= +0
+    if (r2i >= sEi[0] && r2i < sEi[kHistBins]) {
+        // bin b: sE[b] <= r2 < sE[b+1]; start from a binary32 estimate
+        const float r2f = approx_f32(r2);
+        int bb = (int)((r2f * rsqrtf(r2f) - sigf) * inv_drf);
+        bb = bb < 0 ? 0 : (bb > kHistBins - 1 ? kHistBins - 1 : bb);
+        while (bb > 0 && r2i < sEi[bb]) --bb;
+        while (bb < kHistBins - 1 && r2i >= sEi[bb + 1]) ++bb;
+        atomicAdd(&sh[bb], 1u);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restrict__ cells,
                                            const double* __restrict__ edges2, unsigned long long* __restrict__ hist,
                                            int bx, int by, int q) {
     __shared__ unsigned int sh[kHistBins];
-    __shared__ double sE[kHistBins + 1];
+    __shared__ long long sEi[kHistBins + 1];   // bit patterns of the squared edges
+    __shared__ uint32_t squeue[kHistBY][kHistQueue];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y) sh[b] = 0u;
-    for (int b = tid; b <= kHistBins; b += blockDim.x * blockDim.y) sE[b] = edges2[b];
+    for (int b = tid; b <= kHistBins; b += blockDim.x * blockDim.y) sEi[b] = __double_as_longlong(edges2[b]);
     __syncthreads();
+    const int lane = threadIdx.x;
     const int hx = bx * kHistBX + threadIdx.x;
     const int hy = by * kHistBY + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
+    uint32_t* sq = squeue[threadIdx.y];
     Cell<T> own;
 #pragma unroll
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = T(kEmpty);
@@ -778,6 +825,7 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
             oy[i] = to_f32(own.y[i]);
             occupied |= own.x[i] >= T(0) ? (0xFu << (4 * i)) : 0u;
         }
+        int qn = 0;   // queued candidates of this warp (warp-uniform)
         for (int dy = -2; dy <= 2; ++dy) {
             for (int dx = -2; dx <= 2; ++dx) {
                 Cell<T> c;
@@ -807,27 +855,30 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
                 // apart), and no disk is paired with itself
                 cand &= occupied;
                 if (dx == 0 && dy == 0) cand &= ~0x8421u;
-                while (cand) {
-                    const int b = __ffs(cand) - 1;
-                    cand &= cand - 1;
-                    const int i = b >> 2, j = b & 3;
-                    const double px = (double)pick(own.x, i), py = (double)pick(own.y, i);
-                    const double ex = __dadd_rn((double)pick(c.x, j), (double)dx * wxd);
-                    const double ey = __dadd_rn((double)pick(c.y, j), (double)dy * wyd);
-                    const double ddx = __dsub_rn(px, ex), ddy = __dsub_rn(py, ey);
-                    const double r2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
-                    if (r2 >= sE[0] && r2 < sE[kHistBins]) {
-                        // bin b: sE[b] <= r2 < sE[b+1]; start from a binary32 estimate
-                        const float r2f = approx_f32(r2);
-                        int bb = (int)((r2f * rsqrtf(r2f) - sigf) * inv_drf);
-                        bb = bb < 0 ? 0 : (bb > kHistBins - 1 ? kHistBins - 1 : bb);
-                        while (bb > 0 && r2 < sE[bb]) --bb;
-                        while (bb < kHistBins - 1 && r2 >= sE[bb + 1]) ++bb;
-                        atomicAdd(&sh[bb], 1u);
+                for (;;) {   // queue the candidates, one per lane and round
+                    const unsigned act = __ballot_sync(0xffffffffu, cand != 0);
+                    if (!act) break;
+                    if (cand) {
+                        const int b = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        sq[qn + __popc(act & ((1u << lane) - 1u))] = hist_entry(lane, b, dx, dy);
+                    }
+                    qn += __popc(act);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        hist_flush<T>(g, cells, sq, 32, q, bx, hy, sEi, sh, wxd, wyd, sigf, inv_drf);
+                        __syncwarp();
+                        const uint32_t v = lane < qn - 32 ? sq[32 + lane] : 0u;
+                        __syncwarp();
+                        if (lane < qn - 32) sq[lane] = v;
+                        __syncwarp();
+                        qn -= 32;
                     }
                 }
             }
         }
+        __syncwarp();
+        hist_flush<T>(g, cells, sq, qn, q, bx, hy, sEi, sh, wxd, wyd, sigf, inv_drf);
     }
     __syncthreads();
     for (int b = tid; b < kHistBins; b += blockDim.x * blockDim.y)
