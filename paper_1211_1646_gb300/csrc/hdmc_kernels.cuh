@@ -434,6 +434,40 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
                              partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
 }
 
+// Coordinate-type helpers: widths, shift distance, next value below w,
+// explicitly rounded add/sub, exact comparisons.
+template <typename T> struct Prm;
+template <> struct Prm<float> {
+    static __device__ __forceinline__ float wx(const Geometry& g) { return g.wxf; }
+    static __device__ __forceinline__ float wy(const Geometry& g) { return g.wyf; }
+    static __device__ __forceinline__ float ds(const SweepDraw& r) { return r.dsf; }
+    static __device__ __forceinline__ float prev(float w) { return __uint_as_float(__float_as_uint(w) - 1u); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ bool ge0(float x) { return x >= 0.f; }
+    static __device__ __forceinline__ bool lt(float x, float w) { return x < w; }
+};
+template <> struct Prm<double> {
+    static __device__ __forceinline__ double wx(const Geometry& g) { return g.wx; }
+    static __device__ __forceinline__ double wy(const Geometry& g) { return g.wy; }
+    static __device__ __forceinline__ double ds(const SweepDraw& r) { return r.ds; }
+    static __device__ __forceinline__ double prev(double w) {
+        return __longlong_as_double(__double_as_longlong(w) - 1ll);
+    }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    // Comparisons on the integer pipe (binary64 ones are slow on this GPU);
+    // exact for every non-NaN x: ge0(x) == (x >= 0) (the bit patterns of
+    // +0 .. +inf and of -0 are at most 2^63 unsigned), and for w > 0
+    // lt(x, w) == (x < w) (negative x read as a negative integer).
+    static __device__ __forceinline__ bool ge0(double x) {
+        return (unsigned long long)__double_as_longlong(x) <= 0x8000000000000000ull;
+    }
+    static __device__ __forceinline__ bool lt(double x, double w) {
+        return __double_as_longlong(x) < __double_as_longlong(w);
+    }
+};
+
 // ---- binary64 sub-sweep ---------------------------------------------------------------
 // Same algorithm in binary64.  Draws: shuffle by one 32-bit Lemire draw in
 // [0, n!) from the cell's shuffle stream; trial t takes the t-th kept attempt
@@ -452,23 +486,39 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
 constexpr float kOverlapBand = 0x1p-15f;
 constexpr float kCircleBand = 0x1p-18f;
 
+// Exact binary64 overlap test of a trial position against every candidate
+// whose binary32 estimate (the prefilter's own expression, with the upper
+// band edge) says "possibly overlapping"; the others are certainly clear.
+// sigma^2 and r^2 are non-negative, so r^2 < sigma^2 compares bit patterns.
 __device__ __forceinline__ bool exact_trial_hit(const Geometry& g, const double* __restrict__ cells,
                                                   const Neighbourhood& nbh, int hx, int hy, const Cell<double>& own,
-                                                  int i, double tx, double ty) {
+                                                  const float ofx[4], const float ofy[4], int i, double tx, double ty,
+                                                  float txf, float tyf) {
+    const long long s2 = __double_as_longlong(g.sig2);
+    const float nhi = -((float)g.sig2 + kOverlapBand);
     bool hit = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const double ddx = __dsub_rn(tx, own.x[j]), ddy = __dsub_rn(ty, own.y[j]);
-        hit |= (j != i) && (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2);
+        const float ex = __fsub_rn(txf, ofx[j]), ey = __fsub_rn(tyf, ofy[j]);
+        if (j != i && __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, nhi)) < 0.f) {
+            const double ddx = __dsub_rn(tx, own.x[j]), ddy = __dsub_rn(ty, own.y[j]);
+            hit |= __double_as_longlong(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy))) < s2;
+        }
     }
+    const float wxf = (float)g.wx, wyf = (float)g.wy;
     for (int c = 0; c < 8; ++c) {
         Cell<double> a;
         load_cell_ro(cells + 8 * nbh.index(g, c, hx, hy), a);
         const double sx = (double)dir_dx(c) * g.wx, sy = (double)dir_dy(c) * g.wy;
+        const float sxf = (float)dir_dx(c) * wxf, syf = (float)dir_dy(c) * wyf;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const double ddx = __dsub_rn(tx, __dadd_rn(a.x[j], sx)), ddy = __dsub_rn(ty, __dadd_rn(a.y[j], sy));
-            hit |= __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < g.sig2;
+            const float ex = __fsub_rn(txf, __fadd_rn(approx_f32(a.x[j]), sxf));
+            const float ey = __fsub_rn(tyf, __fadd_rn(approx_f32(a.y[j]), syf));
+            if (__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, nhi)) < 0.f) {
+                const double ddx = __dsub_rn(tx, __dadd_rn(a.x[j], sx)), ddy = __dsub_rn(ty, __dadd_rn(a.y[j], sy));
+                hit |= __double_as_longlong(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy))) < s2;
+            }
         }
     }
     return hit;
@@ -511,7 +561,8 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
             n2[c] = approx_f32(__ldg(p + 2));
         }
     }
-    const int n = (own.x[0] >= 0.0) + (own.x[1] >= 0.0) + (own.x[2] >= 0.0) + (own.x[3] >= 0.0);
+    const int n = Prm<double>::ge0(own.x[0]) + Prm<double>::ge0(own.x[1]) + Prm<double>::ge0(own.x[2]) +
+                  Prm<double>::ge0(own.x[3]);
     uint32_t dir23 = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) dir23 |= __any_sync(0xffffffffu, n2[c] >= 0.f) ? (1u << c) : 0u;
@@ -573,7 +624,8 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
             }
             const double tx = __dadd_rn(pick(own.x, i), __dmul_rn(dscaled, (double)mu));
             const double ty = __dadd_rn(pick(own.y, i), __dmul_rn(dscaled, (double)mv));
-            const bool inside = tx >= 0.0 && tx < g.wx && ty >= 0.0 && ty < g.wy;
+            const bool inside = Prm<double>::ge0(tx) && Prm<double>::lt(tx, g.wx) && Prm<double>::ge0(ty) &&
+                                Prm<double>::lt(ty, g.wy);
             const float txf = approx_f32(tx), tyf = approx_f32(ty);
             const f2x tx2 = pk(txf, txf), ty2 = pk(tyf, tyf);
             uint32_t sure = 0, maybe = 0;   // sign bits: certainly / possibly overlapping
@@ -615,7 +667,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
             }
             bool hit = (sure & 0x80000000u) != 0;
             if (inside && !hit && (maybe & 0x80000000u))
-                hit = exact_trial_hit(g, cells, nbh, hx, hy, own, i, tx, ty);
+                hit = exact_trial_hit(g, cells, nbh, hx, hy, own, ofx, ofy, i, tx, ty, txf, tyf);
             const bool ok = inside && !hit;
             put_if(own.x, i, tx, ok);
             put_if(own.y, i, ty, ok);
@@ -638,6 +690,7 @@ k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __
                  partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
+
 // ---- cell shift: Alg. 4 ----------------------------------------------------------------
 // One thread per new cell; grid (set row, set column, set).  New cell c = the
 // disks of old c that stay inside c after the translation by -f*ds (old slot
@@ -645,26 +698,6 @@ k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __
 // (+f*w).  The ownership test is the same expression in the two threads that
 // see a disk, so every disk lands in exactly one cell (Sec. 3.2).  A
 // re-expressed value that rounds onto the upper edge is clamped below it.
-template <typename T> struct Prm;
-template <> struct Prm<float> {
-    static __device__ __forceinline__ float wx(const Geometry& g) { return g.wxf; }
-    static __device__ __forceinline__ float wy(const Geometry& g) { return g.wyf; }
-    static __device__ __forceinline__ float ds(const SweepDraw& r) { return r.dsf; }
-    static __device__ __forceinline__ float prev(float w) { return __uint_as_float(__float_as_uint(w) - 1u); }
-    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-};
-template <> struct Prm<double> {
-    static __device__ __forceinline__ double wx(const Geometry& g) { return g.wx; }
-    static __device__ __forceinline__ double wy(const Geometry& g) { return g.wy; }
-    static __device__ __forceinline__ double ds(const SweepDraw& r) { return r.ds; }
-    static __device__ __forceinline__ double prev(double w) {
-        return __longlong_as_double(__double_as_longlong(w) - 1ll);
-    }
-    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-};
-
 template <typename T>
 __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restrict__ src, T* __restrict__ dst,
                                             const SweepDraw* __restrict__ draw, DevState* __restrict__ st, int bx,
@@ -691,9 +724,9 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     int kept = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (o.x[j] >= T(0)) {
+        if (Prm<T>::ge0(o.x[j])) {
             const T dp = Prm<T>::sub(ax ? o.y[j] : o.x[j], sd);
-            if (dp >= T(0) && dp < w) {
+            if (Prm<T>::ge0(dp) && Prm<T>::lt(dp, w)) {
                 const T vx = ax ? o.x[j] : dp, vy = ax ? dp : o.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
@@ -706,12 +739,12 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (b.x[j] >= T(0)) {
+        if (Prm<T>::ge0(b.x[j])) {
             const T dp = Prm<T>::sub(ax ? b.y[j] : b.x[j], sd);
-            if (!(dp >= T(0) && dp < w)) {
+            if (!(Prm<T>::ge0(dp) && Prm<T>::lt(dp, w))) {
                 T v = Prm<T>::add(dp, sw);
-                v = (v >= w) ? Prm<T>::prev(w) : v;
-                v = (v < T(0)) ? T(0) : v;
+                v = Prm<T>::lt(v, w) ? v : Prm<T>::prev(w);
+                v = Prm<T>::ge0(v) ? v : T(0);
                 const T vx = ax ? b.x[j] : v, vy = ax ? v : b.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
@@ -809,8 +842,8 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = T(kEmpty);
     const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
     if (live) load_cell_ro(cells + 8 * ((long long)q * g.cq + (long long)hy * g.hx + hx), own);
-    const bool any = __any_sync(0xffffffffu, own.x[0] >= T(0));
-    const bool own23 = __any_sync(0xffffffffu, own.x[2] >= T(0));
+    const bool any = __any_sync(0xffffffffu, Prm<T>::ge0(own.x[0]));
+    const bool own23 = __any_sync(0xffffffffu, Prm<T>::ge0(own.x[2]));
     if (any) {
         const double wxd = (double)Prm<T>::wx(g), wyd = (double)Prm<T>::wy(g);
         const float wxf = (float)Prm<T>::wx(g), wyf = (float)Prm<T>::wy(g);
@@ -823,7 +856,7 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
         for (int i = 0; i < 4; ++i) {
             ox[i] = to_f32(own.x[i]);
             oy[i] = to_f32(own.y[i]);
-            occupied |= own.x[i] >= T(0) ? (0xFu << (4 * i)) : 0u;
+            occupied |= Prm<T>::ge0(own.x[i]) ? (0xFu << (4 * i)) : 0u;
         }
         int qn = 0;   // queued candidates of this warp (warp-uniform)
         for (int dy = -2; dy <= 2; ++dy) {
@@ -838,7 +871,7 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
                 const f2x qy01 = add2(pk(to_f32(c.y[0]), to_f32(c.y[1])), pk(syf, syf));
                 const f2x qy23 = add2(pk(to_f32(c.y[2]), to_f32(c.y[3])), pk(syf, syf));
                 const f2x nt = pk(-thr, -thr);
-                const bool c23 = __any_sync(0xffffffffu, c.x[2] >= T(0));
+                const bool c23 = __any_sync(0xffffffffu, Prm<T>::ge0(c.x[2]));
                 uint32_t cand = 0;   // bit 4i+j: pair (own i, neighbour slot j) passes the estimate
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
