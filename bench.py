@@ -88,6 +88,25 @@ def profiled_traffic(summary="subsweep_f32_n1m.md"):
     return int(t.group(1))
 
 
+# ALU work of one binary32 trial move (Alg. 2), in 32-bit lane operations
+# (an FMA is one operation): the trial position against the 36 slots of the
+# 3x3 cell neighbourhood at 5 operations each (2 differences, 2 FMAs, 1
+# compare); trial coordinate and containment test, 2 FMAs and 4 compares;
+# the random stream, Philox4x32-10 at 8 operations per round (2 wide
+# multiplies = 4, 2 three-input XORs, 2 key additions) with 6 21-bit fields
+# per block and 2 fields per attempt; 9 operations per attempt for the
+# direction (2 fields extracted, converted and scaled; u*u + v*v and its
+# compare); 4/pi attempts per kept direction.
+ALU_OPS_PER_TRIAL = {
+    "slot_tests": 36 * 5,
+    "trial_and_containment": 6,
+    "philox": 80 * (4 / math.pi) / 3,
+    "directions": 9 * (4 / math.pi),
+}
+LANES_PER_SM = 128      # 32-bit ALU/FMA lanes per SM (4 partitions x 32)
+MAX_SM_MHZ = 2070.0     # GB300 maximum SM clock
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -238,7 +257,15 @@ def run_hdmc(args, rank, world, dist):
     # (the halos of the active cells cover the grid) + the active set's
     # particles written once: 1.25 * N * 8 B (binary32 offsets)
     bytes_sub = 1.25 * w.N * 8
-    achieved = bytes_sub / (ms_sub / 1e3) / 1e9
+    achieved_hbm = bytes_sub / (ms_sub / 1e3) / 1e9
+    # ALU roofline: the state (8 floats per cell, 37 MB) stays in L2 through
+    # a step, and the sub-sweep is bound by the lane-operation rate
+    trials_per_launch = trials / args.steps / (SWEEPS_PER_STEP * 4)
+    ops_per_trial = sum(ALU_OPS_PER_TRIAL.values())
+    achieved_alu = ops_per_trial * trials_per_launch / (ms_sub / 1e3) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or MAX_SM_MHZ
+    alu_peak = sms * LANES_PER_SM * mhz * 1e6 / 1e12
 
     # ---- end to end through the C ABI with host buffers ----
     # Each step loads the system's snapshot from pinned host memory (H2D),
@@ -294,11 +321,15 @@ def run_hdmc(args, rank, world, dist):
         "e2e": {"value": e2e_value, "unit": "trial moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": profiled_traffic(), "kernel": "k_subsweep_f32",
-                     "traffic_note": "ncu dram bytes per launch, caches flushed before the pass",
+        "roofline": {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_hbm / hbm_peak, "traffic": profiled_traffic(), "kernel": "k_subsweep_f32",
+                     "traffic_note": "ncu dram bytes per launch inside a run of sweeps (no cache flush)",
                      "peak_kind": peak_kind, "ms_per_launch": ms_sub,
                      "algorithmic_bytes_per_launch": bytes_sub},
+        "roofline_alu": {"bound": "alu", "achieved": achieved_alu, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved_alu / alu_peak, "kernel": "k_subsweep_f32",
+                         "peak_kind": "derived: %d SMs x %d lanes x %.0f MHz" % (sms, LANES_PER_SM, mhz),
+                         "trials_per_launch": trials_per_launch, "ops_per_trial": ops_per_trial},
         "kernels_ms": {"subsweep_f32": ms_sub, "shift_f32": ms_shift, "draws": ms_draw,
                        "subsweep_f64": ms_sub64, "shift_f64": ms_shift64},
         "fp64": {"value": value64, "unit": "trial moves/s", "ms_per_step": ms64 / max(1, args.fp64_steps),

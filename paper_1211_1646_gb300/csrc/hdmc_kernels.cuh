@@ -69,21 +69,6 @@ __device__ __forceinline__ float sym21(uint32_t f) {
     return (float)((int32_t)(2 * f + 1) - (1 << 21)) * 0x1p-21f;
 }
 
-// Uniform permutation of n <= 4 slots from k in [0, n!): Fisher-Yates swaps
-// j <-> k mod (j+1), k /= (j+1), for j = n-1 down to 1.  Returned packed: byte
-// j = old slot that moves to slot j.
-__device__ __forceinline__ uint32_t perm_from_index(int n, uint32_t k) {
-    uint32_t pk = 0x03020100u;
-    auto swap = [&](int a, int b) {
-        const uint32_t va = (pk >> (8 * a)) & 0xFFu, vb = (pk >> (8 * b)) & 0xFFu;
-        pk &= ~((0xFFu << (8 * a)) | (0xFFu << (8 * b)));
-        pk |= (va << (8 * b)) | (vb << (8 * a));
-    };
-    if (n >= 4) { swap(3, (int)(k & 3u)); k >>= 2; }
-    if (n >= 3) { swap(2, (int)(k % 3u)); k /= 3u; }
-    if (n >= 2) { swap(1, (int)(k & 1u)); }
-    return pk;
-}
 
 __device__ __forceinline__ uint32_t factorial(int n) { return n == 4 ? 24u : n == 3 ? 6u : n == 2 ? 2u : 1u; }
 
@@ -135,13 +120,39 @@ __device__ __forceinline__ void put_if(T a[4], int i, T v, bool p) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) a[j] = (p && i == j) ? v : a[j];
 }
+// Swap slot J (compile time) with slot s <= J of both coordinate arrays.
+template <int J, typename T>
+__device__ __forceinline__ void swap_slot(T x[4], T y[4], int s) {
+    T xs = x[J], ys = y[J];
+#pragma unroll
+    for (int m = 0; m < J; ++m) {
+        xs = s == m ? x[m] : xs;
+        ys = s == m ? y[m] : ys;
+    }
+    const T xj = x[J], yj = y[J];
+#pragma unroll
+    for (int m = 0; m < J; ++m) {
+        x[m] = s == m ? xj : x[m];
+        y[m] = s == m ? yj : y[m];
+    }
+    x[J] = xs;
+    y[J] = ys;
+}
+
+// Uniform shuffle of the n <= 4 occupied slots (Alg. 1, the disks of a cell)
+// from one draw k in [0, n!): Fisher-Yates swaps of slot j with slot
+// k mod (j+1), k /= (j+1), for j = n-1 down to 1, applied to the
+// coordinates in place (a swap whose j is not below n is skipped).
 template <typename T>
-__device__ __forceinline__ void permute(T a[4], uint32_t pk) {
-    T r[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) r[j] = pick(a, (int)((pk >> (8 * j)) & 0xFFu));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = r[j];
+__device__ __forceinline__ void shuffle_slots(T x[4], T y[4], int n, uint32_t k) {
+    const int s3 = n >= 4 ? (int)(k & 3u) : 3;
+    const uint32_t k1 = n >= 4 ? k >> 2 : k;
+    const int s2 = n >= 3 ? (int)(k1 % 3u) : 2;
+    const uint32_t k2 = n >= 3 ? k1 / 3u : k1;
+    const int s1 = n >= 2 ? (int)(k2 & 1u) : 1;
+    swap_slot<3>(x, y, s3);
+    swap_slot<2>(x, y, s2);
+    swap_slot<1>(x, y, s1);
 }
 
 __device__ __forceinline__ int wrap(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
@@ -329,9 +340,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | ((uint32_t)Q << 24));
                 kk = s.bounded(range);
             }
-            const uint32_t pk = perm_from_index(n, kk);
-            permute(own.x, pk);
-            permute(own.y, pk);
+            shuffle_slots(own.x, own.y, n, kk);
         }
         float sx0[4], sy0[4];
         if (TRACK) {
@@ -373,7 +382,11 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 const float2 uv = sdir[tt][tid];
                 const float tx = __fmaf_rn(df, uv.x, pick(own.x, i));
                 const float ty = __fmaf_rn(df, uv.y, pick(own.y, i));
-                const bool inside = tx >= 0.f && tx < g.wxf && ty >= 0.f && ty < g.wyf;
+                // tx >= 0 && tx < w as one unsigned compare of the bit
+                // patterns (w > 0); exact because fma(d, u, p) with
+                // d*u != 0 is never -0, the one value read differently
+                const bool inside = __float_as_uint(tx) < __float_as_uint(g.wxf) &&
+                                    __float_as_uint(ty) < __float_as_uint(g.wyf);
                 const f2x tx2 = pk(tx, tx), ty2 = pk(ty, ty);
                 // own cell: every other occupied slot (slot i excluded)
                 f2x z = zpair(tx2, ty2, pk(own.x[0], own.x[1]), pk(own.y[0], own.y[1]), ns2);
@@ -574,9 +587,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
         const uint32_t setbits = (uint32_t)Q << 24;
         if (n >= 2) {
             WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
-            const uint32_t pk = perm_from_index(n, s.bounded(factorial(n)));
-            permute(own.x, pk);
-            permute(own.y, pk);
+            shuffle_slots(own.x, own.y, n, s.bounded(factorial(n)));
         }
         float ofx[4], ofy[4];   // binary32 truncations of the own slots
 #pragma unroll
