@@ -13,6 +13,8 @@
 //             fma(dx, dx, fma(dy, dy, -sigma^2)) < 0.
 #pragma once
 
+#include <utility>
+
 #include "hdmc_device.cuh"
 
 namespace hdmc {
@@ -119,6 +121,33 @@ template <typename T>
 __device__ __forceinline__ void put_if(T a[4], int i, T v, bool p) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) a[j] = (p && i == j) ? v : a[j];
+}
+
+// pick / put_if when i is known to lie in the slot set M (bit j = slot j).
+template <unsigned M, typename T>
+__device__ __forceinline__ T pick_in(const T a[4], int i) {
+    constexpr int top = (M & 8u) ? 3 : (M & 4u) ? 2 : (M & 2u) ? 1 : 0;
+    T r = a[top];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j != top && ((M >> j) & 1u)) r = (i == j) ? a[j] : r;
+    return r;
+}
+template <unsigned M, typename T>
+__device__ __forceinline__ void put_in(T a[4], int i, T v, bool p) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if ((M >> j) & 1u) a[j] = (p && i == j) ? v : a[j];
+}
+
+// Slots that trial t can visit when the n <= 4 disks are visited cyclically
+// from slot 0: {t mod n : n = 1..4}.
+__host__ __device__ constexpr unsigned trial_slots(int t) {
+    return (1u << (t % 1)) | (1u << (t % 2)) | (1u << (t % 3)) | (1u << (t % 4));
+}
+template <typename F, int... T>
+__device__ __forceinline__ void unrolled_trials(F& f, std::integer_sequence<int, T...>) {
+    (f(T, std::integral_constant<unsigned, trial_slots(T)>{}), ...);
 }
 // Swap slot J (compile time) with slot s <= J of both coordinate arrays.
 template <int J, typename T>
@@ -372,16 +401,15 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
         const float df = g.df;
         const f2x ns2 = pk(-g.sig2f, -g.sig2f);
 
-        // 4. trials
+        // 4. trials; trial tt of the current chunk uses direction sdir[tt]
+        // and slot i, which lies in the slot set M
         int i = 0;
-        for (int t0 = 0; t0 < nsel; t0 += kDirChunk) {
-            const int want = min(kDirChunk, nsel - t0);
-            if (t0 > 0) draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, want, sdir, tid);
-#pragma unroll(NSEL > 0 ? (NSEL < kDirChunk ? NSEL : kDirChunk) : 1)
-            for (int tt = 0; tt < want; ++tt) {
+        auto trial = [&](int tt, auto slots) {
+            constexpr unsigned M = decltype(slots)::value;
+            {
                 const float2 uv = sdir[tt][tid];
-                const float tx = __fmaf_rn(df, uv.x, pick(own.x, i));
-                const float ty = __fmaf_rn(df, uv.y, pick(own.y, i));
+                const float tx = __fmaf_rn(df, uv.x, pick_in<M>(own.x, i));
+                const float ty = __fmaf_rn(df, uv.y, pick_in<M>(own.y, i));
                 // tx >= 0 && tx < w as one unsigned compare of the bit
                 // patterns (w > 0); exact because fma(d, u, p) with
                 // d*u != 0 is never -0, the one value read differently
@@ -390,10 +418,10 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 const f2x tx2 = pk(tx, tx), ty2 = pk(ty, ty);
                 // own cell: every other occupied slot (slot i excluded)
                 f2x z = zpair(tx2, ty2, pk(own.x[0], own.x[1]), pk(own.y[0], own.y[1]), ns2);
-                uint32_t acc = (i == 0 ? 0u : lo32(z)) | (i == 1 ? 0u : hi32(z));
+                uint32_t acc = ((M & 1u) && i == 0 ? 0u : lo32(z)) | ((M & 2u) && i == 1 ? 0u : hi32(z));
                 if (own23) {
                     z = zpair(tx2, ty2, pk(own.x[2], own.x[3]), pk(own.y[2], own.y[3]), ns2);
-                    acc |= (i == 2 ? 0u : lo32(z)) | (i == 3 ? 0u : hi32(z));
+                    acc |= ((M & 4u) && i == 2 ? 0u : lo32(z)) | ((M & 8u) && i == 3 ? 0u : hi32(z));
                 }
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -413,11 +441,21 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                     acc |= lo32(z) | hi32(z);
                 }
                 const bool ok = inside && !(acc & 0x80000000u);
-                put_if(own.x, i, tx, ok);
-                put_if(own.y, i, ty, ok);
+                put_in<M>(own.x, i, tx, ok);
+                put_in<M>(own.y, i, ty, ok);
                 n_acc += ok;
                 n_leave += !inside;
                 i = (i + 1 == n) ? 0 : i + 1;
+            }
+        };
+        if constexpr (NSEL > 0 && NSEL <= kDirChunk) {
+            unrolled_trials(trial, std::make_integer_sequence<int, NSEL>{});
+        } else {
+            for (int t0 = 0; t0 < nsel; t0 += kDirChunk) {
+                const int want = min(kDirChunk, nsel - t0);
+                if (t0 > 0) draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, want, sdir, tid);
+#pragma unroll 1
+                for (int tt = 0; tt < want; ++tt) trial(tt, std::integral_constant<unsigned, 0xFu>{});
             }
         }
         n_tr = (unsigned)nsel;
