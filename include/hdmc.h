@@ -76,7 +76,8 @@ size_t hdmc_workspace_bytes(int64_t N, double Lx, double Ly, double sigma, int p
  * is closest to sqrt(3)/2 of the column spacing), each displaced uniformly
  * within 0.01 sigma, and binned into the cell grid:
  *   mx = largest even integer <= Lx/sigma (likewise my), wx = Lx/mx,
- *   wy = Ly/my; requires mx, my >= 4 and wx, wy < sqrt(2) sigma.
+ *   wy = Ly/my; requires mx, my >= 4, wx, wy < sqrt(2) sigma and
+ *   mx*my < 2^32 (cells are indexed in 32 bits on the device).
  * d is the maximum trial displacement (0 < d < min(wx,wy)/2), nselect the
  * number n_M of trial moves per cell and sub-sweep (1..255), seed the key of
  * every random stream.  precision is HDMC_FP64 or HDMC_FP32_LOCAL.

@@ -43,6 +43,7 @@ int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, doubl
     if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy)) return HDMC_EINVAL;
     if (!(dmove > 0) || !(dmove < 0.5 * wx) || !(dmove < 0.5 * wy)) return HDMC_EINVAL;
     if ((int64_t)mx * my * kSlots < N) return HDMC_EINVAL;
+    if ((int64_t)mx * my >= (int64_t(1) << 32)) return HDMC_EINVAL;   // kernels index cells in 32 bits
     Geometry& g = d.g;
     g = Geometry{};
     g.mx = mx;

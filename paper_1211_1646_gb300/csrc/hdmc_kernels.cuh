@@ -234,15 +234,18 @@ __device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned i
 // neighbours (cx, cy +- 1) in set Q^2 at half-rows yd, yu, the diagonal ones
 // in set Q^3 (periodic wrap on the half grid).  Directions c = 0..7 run over
 // (dx,dy) = (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1).
+// Cell indices are 32-bit here (the grid has fewer than 2^32 cells) and are
+// widened once, in cell_at.
 struct Neighbourhood {
-    long long base[4];   // first cell of set Q, Q^1, Q^2, Q^3
+    uint32_t base[4];   // first cell of set Q, Q^1, Q^2, Q^3
     int xl, xr, yd, yu;
     __device__ Neighbourhood(const Geometry& g, int Q, int hx, int hy) {
         const int qx = Q & 1, qy = Q >> 1;
-        base[0] = (long long)Q * g.cq;
-        base[1] = (long long)(Q ^ 1) * g.cq;
-        base[2] = (long long)(Q ^ 2) * g.cq;
-        base[3] = (long long)(Q ^ 3) * g.cq;
+        const uint32_t cq = (uint32_t)g.cq;
+        base[0] = (uint32_t)Q * cq;
+        base[1] = (uint32_t)(Q ^ 1) * cq;
+        base[2] = (uint32_t)(Q ^ 2) * cq;
+        base[3] = (uint32_t)(Q ^ 3) * cq;
         xl = hx - 1 + qx;
         xl = xl < 0 ? g.hx - 1 : xl;
         xr = hx + qx;
@@ -252,13 +255,20 @@ struct Neighbourhood {
         yu = hy + qy;
         yu = yu >= g.hy ? 0 : yu;
     }
-    __device__ __forceinline__ long long index(const Geometry& g, int c, int hx, int hy) const {
+    __device__ __forceinline__ uint32_t index(const Geometry& g, int c, int hx, int hy) const {
         const int col = (c == 1 || c == 6) ? hx : ((c == 0 || c == 3 || c == 5) ? xl : xr);
         const int row = (c < 3) ? yd : (c < 5 ? hy : yu);
         const int set = (c == 3 || c == 4) ? 1 : ((c == 1 || c == 6) ? 2 : 3);
-        return base[set] + (long long)row * g.hx + col;
+        return base[set] + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col;
+    }
+    __device__ __forceinline__ uint32_t own(const Geometry& g, int hx, int hy) const {
+        return base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx;
     }
 };
+template <typename T>
+__device__ __forceinline__ T* cell_at(T* cells, uint32_t idx) {
+    return cells + 8 * (size_t)idx;
+}
 __device__ __forceinline__ int dir_dx(int c) { return (c == 1 || c == 6) ? 0 : ((c == 0 || c == 3 || c == 5) ? -1 : 1); }
 __device__ __forceinline__ int dir_dy(int c) { return c < 3 ? -1 : (c < 5 ? 0 : 1); }
 
@@ -322,7 +332,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     Cell<float> own;
 #pragma unroll
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = (float)kEmpty;
-    float* ownp = cells + 8 * (nbh.base[0] + (long long)hy * g.hx + hx);
+    float* ownp = cell_at(cells, nbh.own(g, hx, hy));
     if (live) load_cell(ownp, own);
     float4 n01[8];   // slots 0,1 of the neighbours (x0 x1 y0 y1); slot 2 only to flag its use
     float n2[8];
@@ -331,7 +341,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
         n01[c] = make_float4((float)kEmpty, (float)kEmpty, (float)kEmpty, (float)kEmpty);
         n2[c] = (float)kEmpty;
         if (live) {
-            const float* p = cells + 8 * nbh.index(g, c, hx, hy);
+            const float* p = cell_at(cells, nbh.index(g, c, hx, hy));
             const float2 x01 = __ldg(reinterpret_cast<const float2*>(p));
             const float2 y01 = __ldg(reinterpret_cast<const float2*>(p) + 2);
             n01[c] = make_float4(x01.x, x01.y, y01.x, y01.y);
@@ -392,7 +402,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
         const uint32_t more23 = dir23 & (dir23 - 1);
         if (dir23) {
             const int c = __ffs(dir23) - 1;
-            const float2* p = reinterpret_cast<const float2*>(cells + 8 * nbh.index(g, c, hx, hy));
+            const float2* p = reinterpret_cast<const float2*>(cell_at(cells, nbh.index(g, c, hx, hy)));
             const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
             const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
             fx23 = add2(pk(x23.x, x23.y), pk(sx, sx));
@@ -434,7 +444,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 }
                 for (uint32_t m = more23; m; m &= m - 1) {   // warp-uniform, rarely taken
                     const int c = __ffs(m) - 1;
-                    const float2* p = reinterpret_cast<const float2*>(cells + 8 * nbh.index(g, c, hx, hy));
+                    const float2* p = reinterpret_cast<const float2*>(cell_at(cells, nbh.index(g, c, hx, hy)));
                     const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
                     const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
                     z = zpair(tx2, ty2, add2(pk(x23.x, x23.y), pk(sx, sx)), add2(pk(y23.x, y23.y), pk(sy, sy)), ns2);
@@ -559,7 +569,7 @@ __device__ __forceinline__ bool exact_trial_hit(const Geometry& g, const double*
     const float wxf = (float)g.wx, wyf = (float)g.wy;
     for (int c = 0; c < 8; ++c) {
         Cell<double> a;
-        load_cell_ro(cells + 8 * nbh.index(g, c, hx, hy), a);
+        load_cell_ro(cell_at(cells, nbh.index(g, c, hx, hy)), a);
         const double sx = (double)dir_dx(c) * g.wx, sy = (double)dir_dy(c) * g.wy;
         const float sxf = (float)dir_dx(c) * wxf, syf = (float)dir_dy(c) * wyf;
 #pragma unroll
@@ -596,7 +606,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
     Cell<double> own;
 #pragma unroll
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = kEmpty;
-    double* ownp = cells + 8 * (nbh.base[0] + (long long)hy * g.hx + hx);
+    double* ownp = cell_at(cells, nbh.own(g, hx, hy));
     if (live) load_cell(ownp, own);
     float4 n01[8];   // binary32 truncations of neighbour slots 0,1 (x0 x1 y0 y1)
     float n2[8];
@@ -605,7 +615,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
         n01[c] = make_float4((float)kEmpty, (float)kEmpty, (float)kEmpty, (float)kEmpty);
         n2[c] = (float)kEmpty;
         if (live) {
-            const double* p = cells + 8 * nbh.index(g, c, hx, hy);
+            const double* p = cell_at(cells, nbh.index(g, c, hx, hy));
             const double2 x01 = __ldg(reinterpret_cast<const double2*>(p));
             const double2 y01 = __ldg(reinterpret_cast<const double2*>(p) + 2);
             n01[c] = make_float4(approx_f32(x01.x), approx_f32(x01.y), approx_f32(y01.x), approx_f32(y01.y));
@@ -645,7 +655,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
         const uint32_t more23 = dir23 & (dir23 - 1);
         if (dir23) {
             const int c = __ffs(dir23) - 1;
-            const double2* p = reinterpret_cast<const double2*>(cells + 8 * nbh.index(g, c, hx, hy));
+            const double2* p = reinterpret_cast<const double2*>(cell_at(cells, nbh.index(g, c, hx, hy)));
             const double2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
             const float sx = (float)dir_dx(c) * wxf, sy = (float)dir_dy(c) * wyf;
             fx23 = add2(pk(approx_f32(x23.x), approx_f32(x23.y)), pk(sx, sx));
@@ -705,7 +715,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
             }
             for (uint32_t m = more23; m; m &= m - 1) {
                 const int c = __ffs(m) - 1;
-                const double2* p = reinterpret_cast<const double2*>(cells + 8 * nbh.index(g, c, hx, hy));
+                const double2* p = reinterpret_cast<const double2*>(cell_at(cells, nbh.index(g, c, hx, hy)));
                 const double2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
                 const float sx = (float)dir_dx(c) * wxf, sy = (float)dir_dy(c) * wyf;
                 const f2x dx = sub2(tx2, add2(pk(approx_f32(x23.x), approx_f32(x23.y)), pk(sx, sx)));
