@@ -71,19 +71,31 @@ def workload():
     return workloads.n1m_phi0716("fp32")
 
 
+SUBSWEEP_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc_subsweep.cuh")
+
+
+def subsweep_source_hash():
+    """First 16 hex digits of the SHA-256 of the sub-sweep kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in SUBSWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1211_1646_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(summary="subsweep_f32_n1m.md"):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
-    summary, or None when the kernel source changed since the capture."""
-    import hashlib
+    summary, or None when the kernel's sources changed since the capture."""
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        src = open(os.path.join(ROOT, "paper_1211_1646_gb300", "csrc", "hdmc_kernels.cuh"), "rb").read()
+        src_hash = subsweep_source_hash()
     except OSError:
         return None
     t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
     h = re.search(r"kernel_source_sha256_16:\s*(\w+)", text)
-    if not t or not h or h.group(1) != hashlib.sha256(src).hexdigest()[:16]:
+    if not t or not h or h.group(1) != src_hash:
         return None
     return int(t.group(1))
 

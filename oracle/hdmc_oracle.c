@@ -525,7 +525,7 @@ void orc_sweep_draws(uint64_t seed, uint32_t sweep, double wx, double wy, int32_
 
 
 /* ------------------------------------------------------------------------ */
-/* Per-cell random draws of a sub-sweep (Alg. 1 lines 5 and 8).              */
+/* Per-cell random draws of a sub-sweep (Alg. 1: shuffle, trial directions). */
 /*                                                                          */
 /* One cell update (sweep s, set Q, canonical cell c) reads its trial       */
 /* stream T = (s, c, (1<<28)|(Q<<24)) and, for binary64 shuffles or a      */
@@ -700,7 +700,7 @@ void orc_decode_perm(int n, uint32_t k, int32_t out[4])
     for (int j = 0; j < 4; ++j) out[j] = p[j];
 }
 
-/* Slot visited by trial t of a cell holding n disks: t mod n (Alg. 1 line 7). */
+/* Slot visited by trial t of a cell holding n disks: t mod n (Alg. 1).      */
 static int visit_slot(int t, int n) { return t % n; }
 
 void orc_visit_sequence(int n, int nsel, int32_t *seq)
@@ -709,7 +709,7 @@ void orc_visit_sequence(int n, int nsel, int32_t *seq)
 }
 
 /* ------------------------------------------------------------------------ */
-/* One cell update of a sub-sweep (Alg. 1 lines 5-11, Alg. 2)                */
+/* One cell update of a sub-sweep (Alg. 1, Alg. 2)                          */
 /* ------------------------------------------------------------------------ */
 static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, uint64_t acc[4])
 {
@@ -720,7 +720,7 @@ static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
     int perm[4];
     double U[256], V[256];
     cell_draws64(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, perm, U, V);
-    /* shuffle the cell's particles (Alg. 1 line 5) */
+    /* shuffle the cell's particles (Alg. 1) */
     double tx[4], ty[4];
     for (int j = 0; j < n; ++j) { tx[j] = X[perm[j]]; ty[j] = Y[perm[j]]; }
     for (int j = 0; j < n; ++j) { X[j] = tx[j]; Y[j] = ty[j]; }
@@ -802,7 +802,8 @@ static void cell_update32(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
 }
 
 /* All cells of checkerboard set Q (Eq. 1: Q = (cx mod 2) + 2 (cy mod 2)),
- * i.e. lines 4-13 of Alg. 1.  Cells of one set are independent. */
+ * i.e. the cell updates of one set in Alg. 1.  Cells of one set are
+ * independent. */
 static void subsweep(oracle_t *o, uint32_t sweep, int Q)
 {
     int qx = Q & 1, qy = Q >> 1;

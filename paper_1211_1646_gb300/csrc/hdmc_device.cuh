@@ -5,10 +5,11 @@
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
 // the 64-bit seed.  Every random decision of the method reads its own
 // stream, block b of which is Philox(key, (c0, c1, c2, b)):
-//   sweep-level draws of sweep s (Alg. 1 lines 2, 15-16):
+//   sweep-level draws of sweep s (Alg. 1: set order, shift):
 //                      (s, 0xFFFFFFFF, 2<<28)
-//   trial stream of the update of cell c in sweep s, set Q (Alg. 1 lines
-//   5 and 8):          (s, c, (1<<28)|(Q<<24))
+//   trial stream of the update of cell c in sweep s, set Q (Alg. 1:
+//   shuffle draw, trial directions):
+//                      (s, c, (1<<28)|(Q<<24))
 //   shuffle stream of that update (binary64 shuffles; binary32 fallback):
 //                      (s, c, (0<<28)|(Q<<24))
 //   start jitter of disk p:  (p, 0xFFFFFFFE, 3<<28)

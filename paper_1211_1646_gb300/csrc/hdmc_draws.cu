@@ -1,4 +1,4 @@
-// Sweep-level draws (Alg. 1 lines 2 and 15-16) computed on the device, so that
+// Sweep-level draws (Alg. 1: set order and grid shift) computed on the device, so that
 // a recorded graph of many sweeps advances its own sweep counter.
 #include "hdmc_device.cuh"
 
