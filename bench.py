@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="hdmc", choices=["hdmc", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the binary64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-replica batch leg")
     ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -193,7 +194,7 @@ def gpu_identifier(torch, dev):
 def run_hdmc(args, rank, world, dist):
     import numpy as np
     import torch
-    from paper_1211_1646_gb300 import build, hdmc
+    from paper_1211_1646_gb300 import build, hdmc, workloads
 
     build.build()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -310,6 +311,35 @@ def run_hdmc(args, rank, world, dist):
     ms_sub64, ms_shift64, _ = hdmc.hdmc_profile_sweeps(s64.h, 2)
     s64.close()
 
+    # ---- 64 batched replicas of uneven N and phi in one launch per stage ----
+    batch = None
+    if not args.no_batch:
+        reps = workloads.batch64()
+        b = hdmc.Batch(reps, precision="fp32", device=dev)
+        rows, nm = b.autotune(16)
+        for _ in range(max(1, args.warmup)):
+            one_step(b)
+        torch.cuda.synchronize(dev)
+        c0 = int(b.counters()[:, 0].sum())
+        ms_b = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step(b)
+            e1.record(stream)
+            e1.synchronize()
+            ms_b += e0.elapsed_time(e1)
+        tb = int(b.counters()[:, 0].sum()) - c0
+        ms_b = max_over_ranks(ms_b)
+        batch = {"value": sum_over_ranks(tb) / (ms_b / 1e3), "unit": "trial moves/s",
+                 "ms_per_step": ms_b / args.steps, "replicas": len(reps), "N_total": sum(r.N for r in reps),
+                 "rows_per_block": rows, "nselect": nm,
+                 "workload": "64 replicas, N log-uniform in [4096, 262144], phi uniform in [0.60, 0.74], "
+                             "d = 0.08, autotuned (16 sweeps per candidate)"}
+        b.close()
+
     launches_per_step = KERNELS_PER_SWEEP * SWEEPS_PER_STEP + math.ceil(SWEEPS_PER_STEP / GRAPH_CHUNK) + 1
     line = {
         "metric": METRIC,
@@ -347,6 +377,7 @@ def run_hdmc(args, rank, world, dist):
         "fp64": {"value": value64, "unit": "trial moves/s", "ms_per_step": ms64 / max(1, args.fp64_steps),
                  "steps": args.fp64_steps},
         "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
+        "batch64": batch,
         "pressure_betaP_over_rho_last": press[-1] if press else None,
     }
     return line
