@@ -149,12 +149,12 @@ int hdmc_set_state(hdmc_t *h, const double *local, const uint8_t *counts, const 
  *
  * A snapshot is a byte image of the complete state of a system in the
  * library's own device layout: a 256-byte header (magic "HDMCSNP1", format
- * version, precision, N, box, sigma, move size d, n_M, seed, grid, sweep
- * and shift counters, accumulated sample count), then, each at a 256-byte
- * aligned offset, the device state word (grid origin, next sweep/shift
- * index), the trial counters, the histogram accumulator and the cells
- * (set-major, 4 slots per cell in the handle's coordinate type).  Images are
- * portable between hosts of the same byte order.
+ * version, precision, N, box, sigma, move size d, n_M, grid, seed, balance
+ * controls, sweep and shift counters, accumulated sample count), then, each
+ * at a 256-byte aligned offset, the device state word (grid origin, next
+ * sweep/shift index), the trial counters, the histogram accumulator and the
+ * cells (set-major, 4 slots per cell in the handle's coordinate type).
+ * Images are portable between hosts of the same byte order.
  *
  * hdmc_snapshot_bytes returns the image size of this handle, or 0 for a
  * NULL handle. */
@@ -168,8 +168,9 @@ size_t hdmc_snapshot_bytes(const hdmc_t *h);
 int hdmc_save(hdmc_t *h, void *buf, size_t bytes);
 
 /* Restores a snapshot written by hdmc_save for a system of the same N, box,
- * sigma and precision (d, n_M and seed are taken from the image).  The cells
- * are copied to the device and checked there before anything is replaced:
+ * sigma and precision (d, n_M, seed and the balance controls are taken
+ * from the image).  The cells are copied to the device and checked there
+ * before anything is replaced:
  * an image with a wrong header, an occupied slot after an empty one, a
  * coordinate outside [0,w) (or NaN), an unused slot not holding
  * HDMC_EMPTY_SLOT, or a disk total other than N is rejected with
@@ -191,6 +192,25 @@ int hdmc_info(hdmc_t *h, int32_t *mx, int32_t *my, double *wx, double *wy, uint6
 /* Changes the maximum trial displacement d (0 < d < min(wx,wy)/2) for the
  * sweeps enqueued after this call. */
 int hdmc_set_move_size(hdmc_t *h, double d);
+
+/* Balance controls of Table 1 (Sec. 2.4), for negative controls only:
+ * shuffle_particles = 0 skips the shuffle of the disks of each cell before
+ * its trial moves, shuffle_sets = 0 takes the checkerboard sets in the fixed
+ * order 0, 1, 2, 3 instead of a random order per sweep.  Both default to 1
+ * (the method); the random streams are consumed as with both on.  Applies
+ * to the sweeps enqueued after this call. */
+int hdmc_set_balance(hdmc_t *h, int shuffle_particles, int shuffle_sets);
+
+/* Move-size tuning.  d is a free parameter of the method (Sec. 3.3); this
+ * sets it for a target acceptance ratio in a pre-run that advances the
+ * chain: `sweeps` sweeps in rounds of `every`, after each round
+ *   a = accepted / attempted trial moves of the round,
+ *   f = sqrt(a / target) limited to [0.5, 2] (2 if nothing was attempted),
+ *   d <- d * f limited to [1e-6 sigma, 0.49 min(wx, wy)]
+ * (binary64, in this order), then d stays fixed.  The final d is written to
+ * d_out (nullable).  0 < target < 1, sweeps >= 1, every >= 1, else
+ * HDMC_EINVAL.  Synchronises. */
+int hdmc_tune_move_size(hdmc_t *h, double target, int64_t sweeps, int64_t every, double *d_out);
 
 /* Uses stream (a cudaStream_t; NULL = legacy default stream) from now on. */
 int hdmc_set_stream(hdmc_t *h, void *stream);
@@ -256,6 +276,10 @@ int hdmc_batch_set_nselect(hdmc_batch_t *b, const int32_t *nselect);
 /* Sets the sub-sweep block height (2, 4 or 8 rows of 32 active cells;
  * binary32 batches only).  Results do not depend on it.  Synchronises. */
 int hdmc_batch_set_rows(hdmc_batch_t *b, int32_t rows_per_block);
+
+/* Per-replica balance controls, as hdmc_set_balance: shuffle_particles[R],
+ * shuffle_sets[R] (host).  Synchronises. */
+int hdmc_batch_set_balance(hdmc_batch_t *b, const int32_t *shuffle_particles, const int32_t *shuffle_sets);
 
 /* Current launch configuration: cells per block row count of the sub-sweep
  * (block = 32 x rows active cells) and n_M of every replica (nselect[R]). */

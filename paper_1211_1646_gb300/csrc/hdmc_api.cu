@@ -482,7 +482,7 @@ struct SnapHeader {
     int64_t N;
     double Lx, Ly, sigma, d;
     int32_t nsel, mx, my, nblocks;
-    uint32_t key0, key1;
+    uint32_t key0, key1, flags, pad;
     uint64_t sweeps, shifts;
     int64_t n_samples;
     uint64_t off_state, off_partial, off_hist, off_cells, total;
@@ -533,6 +533,7 @@ int hdmc_save(hdmc_t* h, void* buf, size_t bytes) {
     hd.nblocks = h->lay.nblocks;
     hd.key0 = h->g.key0;
     hd.key1 = h->g.key1;
+    hd.flags = h->g.flags;
     hd.sweeps = h->sweeps;
     hd.shifts = h->shifts;
     hd.n_samples = h->n_samples;
@@ -574,7 +575,7 @@ int hdmc_load(hdmc_t* h, const void* buf, size_t bytes) {
                       hd.off_cells == L.cells && hd.total == L.total;
     if (!same) return HDMC_EINVAL;
     if (hd.nsel < 1 || hd.nsel > 255 || !(hd.d > 0) || !(hd.d < 0.5 * g.wx) || !(hd.d < 0.5 * g.wy) ||
-        hd.n_samples < 0)
+        hd.n_samples < 0 || (hd.flags & ~(kNoParticleShuffle | kNoSetShuffle)) != 0)
         return HDMC_EINVAL;
     DevState ds;
     std::memcpy(&ds, b + L.state, sizeof(ds));
@@ -611,7 +612,8 @@ int hdmc_load(hdmc_t* h, const void* buf, size_t bytes) {
     h->sweeps = hd.sweeps;
     h->shifts = hd.shifts;
     h->n_samples = hd.n_samples;
-    if (hd.d != g.d || hd.nsel != g.nsel || hd.key0 != g.key0 || hd.key1 != g.key1) {
+    if (hd.d != g.d || hd.nsel != g.nsel || hd.key0 != g.key0 || hd.key1 != g.key1 || hd.flags != g.flags) {
+        h->g.flags = hd.flags;
         h->g.d = hd.d;
         h->g.df = (float)hd.d;
         h->g.nsel = hd.nsel;
@@ -661,6 +663,38 @@ int hdmc_set_move_size(hdmc_t* h, double d) {
     h->g.df = (float)d;
     h->drop_graphs();   // recorded kernels carry the old value
     return HDMC_OK;
+}
+
+int hdmc_set_balance(hdmc_t* h, int shuffle_particles, int shuffle_sets) {
+    if (!h) return HDMC_EINVAL;
+    const uint32_t f = (shuffle_particles ? 0u : kNoParticleShuffle) | (shuffle_sets ? 0u : kNoSetShuffle);
+    if (f != h->g.flags) {
+        h->g.flags = f;
+        h->drop_graphs();   // recorded kernels carry the old geometry
+    }
+    return HDMC_OK;
+}
+
+int hdmc_tune_move_size(hdmc_t* h, double target, int64_t sweeps, int64_t every, double* d_out) {
+    if (!h || !(target > 0.0) || !(target < 1.0) || sweeps < 1 || every < 1) return HDMC_EINVAL;
+    const double dmax = 0.49 * std::min(h->g.wx, h->g.wy);
+    const double dmin = 1e-6 * h->g.sigma;
+    uint64_t c0[4], c1[4];
+    int e = hdmc_counters(h, c0);
+    for (int64_t done = 0; !e && done < sweeps; done += every) {
+        e = hdmc_sweep(h, std::min(every, sweeps - done));
+        if (!e) e = hdmc_counters(h, c1);
+        if (e) break;
+        const uint64_t tr = c1[0] - c0[0], ac = c1[1] - c0[1];
+        double f = 2.0;
+        if (tr > 0) f = std::sqrt(((double)ac / (double)tr) / target);
+        f = std::min(std::max(f, 0.5), 2.0);
+        const double d = std::min(std::max(h->g.d * f, dmin), dmax);
+        e = hdmc_set_move_size(h, d);
+        for (int k = 0; k < 4; ++k) c0[k] = c1[k];
+    }
+    if (!e && d_out) *d_out = h->g.d;
+    return e;
 }
 
 int hdmc_set_stream(hdmc_t* h, void* stream) {

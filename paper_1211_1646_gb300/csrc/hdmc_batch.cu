@@ -454,6 +454,15 @@ int hdmc_batch_set_nselect(hdmc_batch_t* b, const int32_t* nselect) {
     return upload_layout(b, b->rows);   // descriptors are read at run time: recorded graphs stay valid
 }
 
+int hdmc_batch_set_balance(hdmc_batch_t* b, const int32_t* shuffle_particles, const int32_t* shuffle_sets) {
+    if (!b || !shuffle_particles || !shuffle_sets) return HDMC_EINVAL;
+    int e = cuda_code(cudaStreamSynchronize(b->stream));
+    if (e) return e;
+    for (int r = 0; r < b->R; ++r)
+        b->sys[r].g.flags = (shuffle_particles[r] ? 0u : kNoParticleShuffle) | (shuffle_sets[r] ? 0u : kNoSetShuffle);
+    return upload_layout(b, b->rows);   // descriptors are read at run time: recorded graphs stay valid
+}
+
 int hdmc_batch_set_rows(hdmc_batch_t* b, int32_t rows_per_block) {
     if (!b || (rows_per_block != 2 && rows_per_block != 4 && rows_per_block != 8)) return HDMC_EINVAL;
     if (b->prec != HDMC_FP32_LOCAL && rows_per_block != 4) return HDMC_EINVAL;

@@ -51,7 +51,13 @@ struct Geometry {
     float df;              // its binary32 rounding
     int nsel;              // trial moves per cell and sub-sweep (n_M)
     uint32_t key0, key1;   // Philox key = seed
+    uint32_t flags;        // kNoParticleShuffle | kNoSetShuffle (Table 1 controls); 0 = the method
 };
+
+// Balance controls of Table 1 (Sec. 2.4): skip the shuffle of the disks of a
+// cell, or take the checkerboard sets in the fixed order 0, 1, 2, 3.  The
+// random streams are consumed exactly as with the controls off.
+constexpr uint32_t kNoParticleShuffle = 1u, kNoSetShuffle = 2u;
 
 // Draws of one sweep (Alg. 1): set order, shift direction and distance.
 struct alignas(16) SweepDraw {
@@ -172,6 +178,8 @@ __host__ __device__ inline SweepDraw make_draw(const Geometry& g, uint32_t index
             p[k] = t;
         }
     }
+    if (g.flags & kNoSetShuffle)
+        for (int q = 0; q < 4; ++q) p[q] = q;
     r.fdir = (int32_t)s.bounded(4u);
     const uint32_t hi = s.next(), lo = s.next();
     const double w = (r.fdir >> 1) ? g.wy : g.wx;

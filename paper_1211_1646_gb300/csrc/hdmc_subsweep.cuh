@@ -111,7 +111,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     float net2 = 0.f;
     if (n > 0) {
         // shuffle of the cell's disks (Alg. 1): one draw in [0, n!) by 21-bit Lemire on field 0
-        if (n >= 2) {
+        if (n >= 2 && !(g.flags & kNoParticleShuffle)) {
             const uint32_t range = factorial(n);
             const uint32_t m = f0 * range;
             const uint32_t thr = n == 4 ? 8u : (n == 3 ? 2u : 0u);   // 2^21 mod n!
@@ -340,7 +340,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
     if (n > 0) {
         const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
         const uint32_t setbits = (uint32_t)Q << 24;
-        if (n >= 2) {
+        if (n >= 2 && !(g.flags & kNoParticleShuffle)) {
             WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);
             shuffle_slots(own.x, own.y, n, s.bounded(factorial(n)));
         }

@@ -50,6 +50,8 @@ SIGNATURES = {
     "hdmc_counters": (ctypes.c_int, [_vp, _u64p]),
     "hdmc_info": (ctypes.c_int, [_vp, _i32p, _i32p, _f64p, _f64p, _u64p, _u64p, _f64p]),
     "hdmc_set_move_size": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "hdmc_tune_move_size": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _f64p]),
+    "hdmc_set_balance": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "hdmc_set_stream": (ctypes.c_int, [_vp, _vp]),
     "hdmc_sync": (ctypes.c_int, [_vp]),
     "hdmc_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p, _f64p]),
@@ -67,6 +69,7 @@ SIGNATURES = {
     "hdmc_batch_info": (ctypes.c_int, [_vp, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _u64p, _f64p]),
     "hdmc_batch_set_nselect": (ctypes.c_int, [_vp, _i32p]),
     "hdmc_batch_set_rows": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "hdmc_batch_set_balance": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "hdmc_batch_config": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "hdmc_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, _i32p]),
     "hdmc_batch_destroy": (None, [_vp]),
@@ -233,6 +236,16 @@ def hdmc_set_move_size(h, d):
     _check(lib().hdmc_set_move_size(h, d), "hdmc_set_move_size")
 
 
+def hdmc_set_balance(h, shuffle_particles, shuffle_sets):
+    _check(lib().hdmc_set_balance(h, int(bool(shuffle_particles)), int(bool(shuffle_sets))), "hdmc_set_balance")
+
+
+def hdmc_tune_move_size(h, target, sweeps, every):
+    d = ctypes.c_double()
+    _check(lib().hdmc_tune_move_size(h, target, sweeps, every, ctypes.byref(d)), "hdmc_tune_move_size")
+    return d.value
+
+
 def hdmc_set_stream(h, stream):
     _check(lib().hdmc_set_stream(h, stream), "hdmc_set_stream")
 
@@ -335,6 +348,12 @@ def hdmc_batch_set_nselect(b, nselect):
 
 def hdmc_batch_set_rows(b, rows):
     _check(lib().hdmc_batch_set_rows(b, rows), "hdmc_batch_set_rows")
+
+
+def hdmc_batch_set_balance(b, shuffle_particles, shuffle_sets):
+    p = np.ascontiguousarray([int(bool(v)) for v in shuffle_particles], dtype=np.int32)
+    q = np.ascontiguousarray([int(bool(v)) for v in shuffle_sets], dtype=np.int32)
+    _check(lib().hdmc_batch_set_balance(b, _p(p, _i32p), _p(q, _i32p)), "hdmc_batch_set_balance")
 
 
 def hdmc_batch_config(b, R):
@@ -447,6 +466,14 @@ class System:
     def set_move_size(self, d):
         hdmc_set_move_size(self.h, d)
 
+    def set_balance(self, shuffle_particles=True, shuffle_sets=True):
+        """Table 1 negative controls (both True = the method)."""
+        hdmc_set_balance(self.h, shuffle_particles, shuffle_sets)
+
+    def tune_move_size(self, target=0.30, sweeps=1000, every=100):
+        """Pre-run that sets d for the target acceptance ratio; returns d."""
+        return hdmc_tune_move_size(self.h, target, sweeps, every)
+
     def sync(self):
         hdmc_sync(self.h)
 
@@ -516,6 +543,12 @@ class Batch:
 
     def set_rows(self, rows):
         hdmc_batch_set_rows(self.b, rows)
+
+    def set_balance(self, shuffle_particles, shuffle_sets):
+        """Per-replica Table 1 negative controls (sequences of R booleans)."""
+        if len(shuffle_particles) != self.R or len(shuffle_sets) != self.R:
+            raise ValueError("one value per replica")
+        hdmc_batch_set_balance(self.b, shuffle_particles, shuffle_sets)
 
     def set_nselect(self, nselect):
         hdmc_batch_set_nselect(self.b, nselect)

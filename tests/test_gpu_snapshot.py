@@ -17,9 +17,9 @@ from paper_1211_1646_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 PREC = {"fp64": O.FP64, "fp32": O.FP32}
-HEADER = struct.Struct("<8sIIq4d4i2I2Qq5Q")
-FIELDS = ("magic version precision N Lx Ly sigma d nsel mx my nblocks key0 key1 sweeps shifts n_samples "
-          "off_state off_partial off_hist off_cells total").split()
+HEADER = struct.Struct("<8sIIq4d4i4I2Qq5Q")
+FIELDS = ("magic version precision N Lx Ly sigma d nsel mx my nblocks key0 key1 flags pad sweeps shifts "
+          "n_samples off_state off_partial off_hist off_cells total").split()
 
 
 @pytest.fixture(scope="module", autouse=True)
