@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the binary64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-replica batch leg")
+    ap.add_argument("--no-n4m", action="store_true", help="skip the N=4M legs")
     ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -311,6 +312,23 @@ def run_hdmc(args, rank, world, dist):
     ms_sub64, ms_shift64, _ = hdmc.hdmc_profile_sweeps(s64.h, 2)
     s64.close()
 
+    # ---- N = 2048^2 at the four densities of that workload (state larger than L2) ----
+    n4m = None
+    if not args.no_n4m:
+        n4m = {}
+        for phi in (0.700, 0.710, 0.716, 0.720):
+            w4 = workloads.n4m(phi)
+            s4 = hdmc.System(w4.N, w4.Lx, w4.Ly, 1.0, w4.d, w4.nselect, seed, "fp32", device=dev)
+            t4, ms4, _ = timed_steps(s4, args.steps, max(1, args.warmup))
+            ms4 = max_over_ranks(ms4)
+            sub4, shift4, _ = hdmc.hdmc_profile_sweeps(s4.h, 8)
+            bytes4 = 1.25 * w4.N * 8
+            n4m["%.3f" % phi] = {
+                "value": sum_over_ranks(t4) / (ms4 / 1e3), "unit": "trial moves/s",
+                "ms_per_step": ms4 / args.steps, "subsweep_ms": sub4, "shift_ms": shift4,
+                "roofline_hbm_frac": bytes4 / (sub4 / 1e3) / 1e9 / hbm_peak}
+            s4.close()
+
     # ---- 64 batched replicas of uneven N and phi in one launch per stage ----
     batch = None
     if not args.no_batch:
@@ -378,6 +396,7 @@ def run_hdmc(args, rank, world, dist):
                  "steps": args.fp64_steps},
         "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
         "batch64": batch,
+        "n4m": n4m,
         "pressure_betaP_over_rho_last": press[-1] if press else None,
     }
     return line
