@@ -135,13 +135,18 @@ int check_device(hdmc_t* h) {
 
 // ---- sweep driver ------------------------------------------------------------
 
+// The draws kernel and the first sub-sweep after it are ordinary launches;
+// every later kernel of the run is a programmatic dependent of the one
+// before it (launch_on), so its blocks fill the SMs that the previous
+// kernel's last blocks leave idle.
 void enqueue_sweeps(hdmc_t* h, cudaStream_t s, int K, int parity) {
-    const LaunchCtx c = h->ctx(s);
+    LaunchCtx c = h->ctx(s);
     launch_draws(c, h->table, K, true);
     for (int j = 0; j < K; ++j) {
         void* a = h->cells[parity ^ (j & 1)];
         void* b = h->cells[parity ^ (j & 1) ^ 1];
         for (int k = 0; k < 4; ++k) {
+            c.pdl = j > 0 || k > 0;
             if (h->prec == HDMC_FP64) launch_subsweep_f64(c, a, h->table + j, k);
             else launch_subsweep_f32(c, a, h->table + j, k);
         }

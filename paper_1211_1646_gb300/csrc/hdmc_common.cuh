@@ -14,6 +14,14 @@
 
 namespace hdmc {
 
+// Programmatic dependent launch (launch_on with c.pdl): pdl_release lets the
+// next kernel of the stream launch once every block of this grid has called
+// it; pdl_wait returns when the previous kernel has completed and its writes
+// are visible (at once for a normal launch).  Kernels launched this way call
+// both before their first memory access.
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr int kDirChunk = 8;   // trial directions drawn ahead per thread (binary32 sub-sweep)
 
 // ---- packed binary32 pairs (Blackwell f32x2 arithmetic, IEEE round-to-nearest per lane) ----

@@ -197,11 +197,35 @@ __host__ __device__ inline SweepDraw make_draw(const Geometry& g, uint32_t index
 struct LaunchCtx {
     Geometry g;
     cudaStream_t stream;
+    bool pdl = false;              // launch as a programmatic dependent of the previous kernel
     DevState* st;
     unsigned long long* partial;   // per-block trial counters, 4 per sub-sweep block
     unsigned long long* hist;      // contact histogram accumulator (kHistBins)
     const double* edges2;          // squared bin edges (sigma + k dr)^2, k = 0..kHistBins
 };
+
+// Launches kernel<<<grid, block>>>(args) on c.stream; with c.pdl, as a
+// programmatic dependent launch: its blocks may be scheduled while the
+// previous kernel of the stream finishes, and wait (griddepcontrol.wait, at
+// the top of every such kernel) for its completion before reading anything.
+template <typename... P, typename... A>
+inline void launch_on(const LaunchCtx& c, void (*kernel)(P...), dim3 grid, dim3 block, A... args) {
+    if (!c.pdl) {
+        kernel<<<grid, block, 0, c.stream>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 void launch_draws(const LaunchCtx& c, SweepDraw* table, int count, bool sweep_mode);
 void launch_draws_batch(cudaStream_t s, const ReplicaDesc* reps, DevState* sts, SweepDraw* table, int R, int count);

@@ -5,9 +5,9 @@ namespace hdmc {
 void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k) {
     float* a = reinterpret_cast<float*>(cells);
     if (c.g.nsel == 4)
-        k_subsweep_f32<4, 4><<<subsweep_grid(c.g), dim3(32, 4), 0, c.stream>>>(c.g, a, draw, k, c.partial);
+        launch_on(c, k_subsweep_f32<4, 4>, subsweep_grid(c.g), dim3(32, 4), c.g, a, draw, k, c.partial);
     else
-        k_subsweep_f32<4, 0><<<subsweep_grid(c.g), dim3(32, 4), 0, c.stream>>>(c.g, a, draw, k, c.partial);
+        launch_on(c, k_subsweep_f32<4, 0>, subsweep_grid(c.g), dim3(32, 4), c.g, a, draw, k, c.partial);
 }
 void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     launch_shift_t<float>(c, src, dst, draw);

@@ -90,6 +90,8 @@ template <typename T>
 __global__ void __launch_bounds__(kShiftBX * kShiftBY)
 k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const SweepDraw* __restrict__ draw,
         DevState* __restrict__ st) {
+    pdl_release();
+    pdl_wait();
     shift_cells<T>(g, src, dst, draw, st, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -320,8 +322,8 @@ inline dim3 set_grid(const Geometry& g, dim3 block) {
 template <typename T>
 void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     const dim3 block(kShiftBX, kShiftBY);
-    k_shift<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(src),
-                                                               reinterpret_cast<T*>(dst), draw, c.st);
+    launch_on(c, k_shift<T>, set_grid(c.g, block), block, c.g, reinterpret_cast<const T*>(src),
+              reinterpret_cast<T*>(dst), draw, c.st);
 }
 
 template <typename T>

@@ -231,6 +231,8 @@ template <int ROWS, int NSEL>
 static __global__ void __launch_bounds__(32 * ROWS, 20 / ROWS)
 k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
+    pdl_release();
+    pdl_wait();
     __shared__ float2 sdir[kDirChunk][32 * ROWS];
     subsweep_f32<ROWS, NSEL>(g, cells, draw, k, blockIdx.x, blockIdx.y,
                              partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
@@ -452,6 +454,8 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
 static __global__ void __launch_bounds__(128, 3)
 k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
+    pdl_release();
+    pdl_wait();
     subsweep_f64(g, cells, draw, k, blockIdx.x, blockIdx.y,
                  partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
 }
