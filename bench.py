@@ -192,6 +192,41 @@ def gpu_identifier(torch, dev):
         return dev
 
 
+class Ranks:
+    """Rank plumbing of a replicas-only run (one process per GPU): each rank
+    advances its own independent system; the only collectives are the
+    barriers around the timed region and the reductions of the reported
+    numbers (max of times, sum of work).  Without a process group every
+    call is the identity."""
+
+    def __init__(self, dist, device):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
+def replica_seed(rank):
+    """Seed of rank r's independent replica."""
+    return 1 + rank
+
+
 def run_hdmc(args, rank, world, dist):
     import numpy as np
     import torch
@@ -202,27 +237,11 @@ def run_hdmc(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload()
-    seed = 1 + rank
+    seed = replica_seed(rank)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    ranks = Ranks(dist, dev)
+    barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     def one_step(sysm):
         sysm.sweep(SWEEPS_PER_STEP)
