@@ -261,8 +261,9 @@ struct Neighbourhood {
     __device__ __forceinline__ uint32_t index(const Geometry& g, int c, int hx, int hy) const {
         const int col = (c == 1 || c == 6) ? hx : ((c == 0 || c == 3 || c == 5) ? xl : xr);
         const int row = (c < 3) ? yd : (c < 5 ? hy : yu);
-        const int set = (c == 3 || c == 4) ? 1 : ((c == 1 || c == 6) ? 2 : 3);
-        return base[set] + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col;
+        // selects, not base[set]: a runtime index would put the array in local memory
+        const uint32_t b = (c == 3 || c == 4) ? base[1] : ((c == 1 || c == 6) ? base[2] : base[3]);
+        return b + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col;
     }
     __device__ __forceinline__ uint32_t own(const Geometry& g, int hx, int hy) const {
         return base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx;

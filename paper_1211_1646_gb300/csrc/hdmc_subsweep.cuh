@@ -451,7 +451,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
     add_block_counters<4>(n_tr, n_acc, n_leave, bpart);
 }
 
-static __global__ void __launch_bounds__(128, 3)
+static __global__ void __launch_bounds__(128, 4)
 k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
     pdl_release();
