@@ -200,34 +200,21 @@ __device__ __forceinline__ float approx_f32(double v) {
     return e < 897u ? __uint_as_float(hi & 0x80000000u) : __uint_as_float(f);
 }
 
-// Per-block trial counters: bpart[{trials, accepted, left, overlap}] of this
-// block's own slot (blocks with the same slot run in stream order, so the
-// read-modify-write needs no atomics).
+// Per-block trial counters bpart[{trials, accepted, left, overlap}] of the
+// block's own slot: each warp adds its sums with fire-and-forget atomic
+// adds (no value returned, so nothing waits on the round trip; integer sums
+// do not depend on their order).
 template <int ROWS>
 __device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned int n_acc, unsigned int n_leave,
                                                    unsigned long long* __restrict__ bpart) {
-    __shared__ unsigned int red[ROWS][3];
     const unsigned a = __reduce_add_sync(0xffffffffu, n_tr);
     const unsigned b = __reduce_add_sync(0xffffffffu, n_acc);
     const unsigned c = __reduce_add_sync(0xffffffffu, n_leave);
-    if (threadIdx.x == 0) {
-        red[threadIdx.y][0] = a;
-        red[threadIdx.y][1] = b;
-        red[threadIdx.y][2] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        unsigned tr = 0, ac = 0, lv = 0;
-#pragma unroll
-        for (int w = 0; w < ROWS; ++w) {
-            tr += red[w][0];
-            ac += red[w][1];
-            lv += red[w][2];
-        }
-        bpart[0] += tr;
-        bpart[1] += ac;
-        bpart[2] += lv;
-        bpart[3] += tr - ac - lv;
+    if (threadIdx.x == 0 && a != 0) {
+        atomicAdd(bpart + 0, (unsigned long long)a);
+        atomicAdd(bpart + 1, (unsigned long long)b);
+        atomicAdd(bpart + 2, (unsigned long long)c);
+        atomicAdd(bpart + 3, (unsigned long long)(a - b - c));
     }
 }
 
