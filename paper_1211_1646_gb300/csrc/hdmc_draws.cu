@@ -44,6 +44,8 @@ void launch_draws_batch(cudaStream_t s, const ReplicaDesc* reps, DevState* sts, 
     k_draws_batch<<<R, 64, 0, s>>>(reps, sts, table, R, count);
 }
 
-dim3 subsweep_grid(const Geometry& g) { return dim3((unsigned)((g.hx + 31) / 32), (unsigned)((g.hy + 3) / 4)); }
+dim3 subsweep_grid(const Geometry& g) {
+    return dim3((unsigned)((g.hx + 31) / 32), (unsigned)((g.hy + kCounterRows - 1) / kCounterRows));
+}
 
 }  // namespace hdmc

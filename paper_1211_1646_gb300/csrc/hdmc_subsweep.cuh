@@ -234,8 +234,10 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
     pdl_release();
     pdl_wait();
     __shared__ float2 sdir[kDirChunk][32 * ROWS];
-    subsweep_f32<ROWS, NSEL>(g, cells, draw, k, blockIdx.x, blockIdx.y,
-                             partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sdir);
+    // counters of the tile that holds this block (shared by the blocks of a
+    // tile: atomic adds)
+    const long long slot = (long long)(blockIdx.y * ROWS / kCounterRows) * gridDim.x + blockIdx.x;
+    subsweep_f32<ROWS, NSEL>(g, cells, draw, k, blockIdx.x, blockIdx.y, partial + 4 * slot, sdir);
 }
 
 // ---- binary64 sub-sweep ---------------------------------------------------------------
