@@ -229,10 +229,9 @@ inline void launch_on(const LaunchCtx& c, void (*kernel)(P...), dim3 grid, dim3 
 
 void launch_draws(const LaunchCtx& c, SweepDraw* table, int count, bool sweep_mode);
 void launch_draws_batch(cudaStream_t s, const ReplicaDesc* reps, DevState* sts, SweepDraw* table, int R, int count);
-// Sub-sweep tiles of 32 set columns x kCounterRows set rows: the binary64
-// kernel's blocks, and the unit of the per-tile trial counters that every
-// sub-sweep adds into (the binary32 kernel runs one-row blocks, four to a
-// tile).
+// Trial-counter tiles of the sub-sweeps: 32 set columns x kCounterRows set
+// rows, one slot of 4 counters each; the sub-sweep kernels run one-row
+// blocks, and the blocks of a tile add into its slot.
 constexpr int kCounterRows = 4;
 dim3 subsweep_grid(const Geometry& g);
 

@@ -3,8 +3,8 @@
 
 namespace hdmc {
 void launch_subsweep_f64(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k) {
-    launch_on(c, k_subsweep_f64, subsweep_grid(c.g), dim3(32, 4), c.g, reinterpret_cast<double*>(cells), draw, k,
-              c.partial);
+    launch_on(c, k_subsweep_f64, dim3((unsigned)((c.g.hx + 31) / 32), (unsigned)c.g.hy), dim3(32, 1), c.g,
+              reinterpret_cast<double*>(cells), draw, k, c.partial);
 }
 void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     launch_shift_t<double>(c, src, dst, draw);

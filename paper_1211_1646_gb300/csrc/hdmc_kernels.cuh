@@ -282,7 +282,7 @@ k_subsweep_f64_batch(const ReplicaDesc* __restrict__ reps, const unsigned short*
     const ReplicaDesc* rd = reps + r;
     const int local = (int)blockIdx.x - rd->sub_block0;
     const int by = local / rd->sub_gx, bx = local - by * rd->sub_gx;
-    subsweep_f64(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
+    subsweep_f64<4>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
                  partial + 4 * (rd->part_off + local));
 }
 

@@ -303,13 +303,14 @@ __device__ __forceinline__ long long sym52_int(uint32_t hi, uint32_t lo) {
 }
 __device__ __forceinline__ float sym52_est(long long m) { return (float)(int)(m >> 29) * 0x1p-23f; }
 
+template <int ROWS>
 __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restrict__ cells,
                                              const SweepDraw* __restrict__ draw, int k, int bx, int by,
                                              unsigned long long* __restrict__ bpart) {
     const int Q = draw->perm[k];
     const uint32_t sweep = draw->sweep;
     const int hx = bx * 32 + threadIdx.x;
-    const int hy = by * 4 + threadIdx.y;
+    const int hy = by * ROWS + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
     const Neighbourhood nbh(g, Q, hx, hy);
@@ -450,16 +451,18 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
         }
         store_cell(ownp, own);
     }
-    add_block_counters<4>(n_tr, n_acc, n_leave, bpart);
+    add_block_counters<ROWS>(n_tr, n_acc, n_leave, bpart);
 }
 
-static __global__ void __launch_bounds__(128, 4)
+// One-warp blocks (one set row of 32 cells), 16 per SM (128 registers).
+static __global__ void __launch_bounds__(32, 16)
 k_subsweep_f64(const Geometry g, double* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
     pdl_release();
     pdl_wait();
-    subsweep_f64(g, cells, draw, k, blockIdx.x, blockIdx.y,
-                 partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+    // counters of the tile that holds this block (shared: atomic adds)
+    subsweep_f64<1>(g, cells, draw, k, blockIdx.x, blockIdx.y,
+                    partial + 4 * ((long long)(blockIdx.y / kCounterRows) * gridDim.x + blockIdx.x));
 }
 
 }  // namespace hdmc
