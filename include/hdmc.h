@@ -273,7 +273,7 @@ int hdmc_batch_info(hdmc_batch_t *b, int r, int32_t *mx, int32_t *my, double *wx
 /* Sets n_M of every replica (host array of R values in 1..255). */
 int hdmc_batch_set_nselect(hdmc_batch_t *b, const int32_t *nselect);
 
-/* Sets the sub-sweep block height (2, 4 or 8 rows of 32 active cells;
+/* Sets the sub-sweep block height (1, 2, 4 or 8 rows of 32 active cells;
  * binary32 batches only).  Results do not depend on it.  Synchronises. */
 int hdmc_batch_set_rows(hdmc_batch_t *b, int32_t rows_per_block);
 
@@ -286,7 +286,7 @@ int hdmc_batch_set_balance(hdmc_batch_t *b, const int32_t *shuffle_particles, co
 int hdmc_batch_config(hdmc_batch_t *b, int32_t *rows_per_block, int32_t *nselect);
 
 /* Autotuner (runs real sweeps, which advance every replica): picks the
- * sub-sweep block height among 32x2, 32x4, 32x8 active cells by the time of
+ * sub-sweep block height among 32x1, 32x2, 32x4, 32x8 active cells by the time of
  * `sweeps` recorded sweeps (binary32 batches), then n_M in {1, 2, 4, 8} (the
  * same for every replica) maximising the net squared displacement per disk
  * and second over `sweeps` sweeps, summed over replicas -- each disk's

@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kChunk = 64;       // sweeps per recorded graph
 constexpr size_t kAlign = 256;
-constexpr int kRowsChoices[3] = {2, 4, 8};
+constexpr int kRowsChoices[4] = {1, 2, 4, 8};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -46,7 +46,7 @@ BatchLayout batch_layout(const std::vector<SysDesc>& sys, int prec) {
     int maxsub = 0, sh = 0, hi = 0;
     for (const SysDesc& d : sys) {
         cells += d.g.C;
-        maxsub += sub_blocks_of(d.g, 2);
+        maxsub += sub_blocks_of(d.g, 1);
         sh += ceil_div(d.g.hx, kShiftBX) * ceil_div(d.g.hy, kShiftBY) * 4;
         hi += ceil_div(d.g.hx, kHistBX) * ceil_div(d.g.hy, kHistBY) * 4;
     }
@@ -464,7 +464,8 @@ int hdmc_batch_set_balance(hdmc_batch_t* b, const int32_t* shuffle_particles, co
 }
 
 int hdmc_batch_set_rows(hdmc_batch_t* b, int32_t rows_per_block) {
-    if (!b || (rows_per_block != 2 && rows_per_block != 4 && rows_per_block != 8)) return HDMC_EINVAL;
+    if (!b || (rows_per_block != 1 && rows_per_block != 2 && rows_per_block != 4 && rows_per_block != 8))
+        return HDMC_EINVAL;
     if (b->prec != HDMC_FP32_LOCAL && rows_per_block != 4) return HDMC_EINVAL;
     return set_rows(b, rows_per_block);
 }

@@ -24,7 +24,8 @@ void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* 
 #define HDMC_SUB_BATCH(ROWS, TRACK)                                                                        \
     k_subsweep_f32_batch<ROWS, TRACK><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(c.reps, c.sub_map, a, draws, \
                                                                                       c.R, j, k, c.partial, c.msd)
-    if (c.rows == 2) { if (track) HDMC_SUB_BATCH(2, true); else HDMC_SUB_BATCH(2, false); }
+    if (c.rows == 1) { if (track) HDMC_SUB_BATCH(1, true); else HDMC_SUB_BATCH(1, false); }
+    else if (c.rows == 2) { if (track) HDMC_SUB_BATCH(2, true); else HDMC_SUB_BATCH(2, false); }
     else if (c.rows == 8) { if (track) HDMC_SUB_BATCH(8, true); else HDMC_SUB_BATCH(8, false); }
     else { if (track) HDMC_SUB_BATCH(4, true); else HDMC_SUB_BATCH(4, false); }
 #undef HDMC_SUB_BATCH

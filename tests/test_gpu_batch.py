@@ -69,7 +69,7 @@ def test_batch_block_layout_does_not_change_results():
     reps = _replicas()
     b = hdmc.Batch(reps, precision="fp32")
     singles = _singles(reps, "fp32")
-    for rows in (2, 8, 4, 2):
+    for rows in (2, 8, 1, 4, 2):
         b.set_rows(rows)
         b.sweep(9)
         for s in singles:
@@ -103,7 +103,7 @@ def test_batch_autotune_and_invariants():
     reps = _replicas()
     b = hdmc.Batch(reps, precision="fp32")
     rows, nm = b.autotune(16)
-    assert rows in (2, 4, 8) and nm in (1, 2, 4, 8)
+    assert rows in (1, 2, 4, 8) and nm in (1, 2, 4, 8)
     assert b.config()[0] == rows and list(b.config()[1]) == [nm] * len(reps)
     b.sweep(40)
     cnt = b.counters()
