@@ -286,13 +286,14 @@ int hdmc_batch_set_balance(hdmc_batch_t *b, const int32_t *shuffle_particles, co
 int hdmc_batch_config(hdmc_batch_t *b, int32_t *rows_per_block, int32_t *nselect);
 
 /* Autotuner (runs real sweeps, which advance every replica): picks the
- * sub-sweep block height among 32x1, 32x2, 32x4, 32x8 active cells by the time of
- * `sweeps` recorded sweeps (binary32 batches), then n_M in {1, 2, 4, 8} (the
- * same for every replica) maximising the net squared displacement per disk
- * and second over `sweeps` sweeps, summed over replicas -- each disk's
- * displacement is taken over its cell update, so confinement to the cell
- * counts against a large n_M (the paper tunes n_M by an autocorrelation time
- * per wall-clock second, Sec. 3.3).  1 <= sweeps <= 4096.  Synchronises. */
+ * sub-sweep block height among 32x1, 32x2, 32x4, 32x8 active cells by the
+ * time of `sweeps` recorded sweeps (binary32 batches), then n_M in
+ * {1, 2, 4, 8} (the same for every replica) maximising the net squared
+ * displacement per disk and second over `sweeps` sweeps, summed over
+ * replicas -- each disk's displacement is taken over its cell update, so
+ * confinement to the cell counts against a large n_M (the paper tunes n_M
+ * by an autocorrelation time per wall-clock second, Sec. 3.3).
+ * 1 <= sweeps <= 4096.  Synchronises. */
 int hdmc_batch_autotune(hdmc_batch_t *b, int64_t sweeps, int32_t *rows_per_block, int32_t *nselect_chosen);
 
 /* Frees the batch (and the workspace if the library allocated it). */
