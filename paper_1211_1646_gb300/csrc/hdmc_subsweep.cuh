@@ -83,10 +83,10 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
         n2[c] = (float)kEmpty;
         if (live) {
             const float* p = cell_at(cells, nbh.index(g, c, hx, hy));
-            const float2 x01 = __ldg(reinterpret_cast<const float2*>(p));
-            const float2 y01 = __ldg(reinterpret_cast<const float2*>(p) + 2);
-            n01[c] = make_float4(x01.x, x01.y, y01.x, y01.y);
-            n2[c] = __ldg(p + 2);
+            Cell<float> a;
+            load_cell_ro(p, a);   // one 256-bit load; slots 0, 1 and x2 are used
+            n01[c] = make_float4(a.x[0], a.x[1], a.y[0], a.y[1]);
+            n2[c] = a.x[2];
         }
     }
 
@@ -103,8 +103,12 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     // 3. cell contents
     const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
     uint32_t dir23 = 0;   // warp-uniform: directions where some lane has a third disk
+    {
+        uint32_t mine = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) dir23 |= __any_sync(0xffffffffu, n2[c] >= 0.f) ? (1u << c) : 0u;
+        for (int c = 0; c < 8; ++c) mine |= (n2[c] >= 0.f) ? (1u << c) : 0u;
+        dir23 = __reduce_or_sync(0xffffffffu, mine);
+    }
     const bool own23 = __any_sync(0xffffffffu, n >= 3);
 
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
