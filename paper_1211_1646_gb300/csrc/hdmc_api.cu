@@ -188,6 +188,7 @@ size_t hdmc_workspace_bytes(int64_t N, double Lx, double Ly, double sigma, int p
     double wx, wy;
     if (N < 1 || (precision != HDMC_FP64 && precision != HDMC_FP32_LOCAL)) return 0;
     if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy)) return 0;
+    if ((int64_t)mx * my >= (int64_t(1) << 32)) return 0;   // as hdmc_create
     Geometry g{};
     g.mx = mx;
     g.my = my;
@@ -309,7 +310,10 @@ int hdmc_profile_sweeps(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_sh
     const int nev = 2;
     cudaEvent_t ev[nev];
     for (int i = 0; i < nev; ++i)
-        if (cudaEventCreate(&ev[i]) != cudaSuccess) return HDMC_ECUDA;
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return HDMC_ECUDA;
+        }
     const LaunchCtx c = h->ctx(h->stream);
     double t_sub = 0, t_shift = 0, t_draw = 0;
     int64_t n_sub = 0, n_shift = 0, n_draw = 0;
