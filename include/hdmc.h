@@ -123,6 +123,20 @@ int hdmc_sample(hdmc_t *h);
  * accumulator.  Synchronises. */
 int hdmc_pressure(hdmc_t *h, double *betaP_over_rho, double *g_contact, uint64_t *hist, int64_t *n_samples);
 
+/* Bond-orientational order parameter psi_6, the order parameter whose
+ * autocorrelation time Sec. 3.3 minimises to tune d and n_M (the paper
+ * cites its definition; this is the usual one): the neighbours k of disk j
+ * are the other disks closer than r_cut, psi_6(j) = (1/n_j) sum_k
+ * exp(6 i theta_jk), computed as z^6 / |z|^6 with z = dx + i dy (0 for a
+ * disk without neighbours).  out[0] + i out[1] = the mean of psi_6(j) over
+ * the N disks, out[2] = the mean of |psi_6(j)|, out[3] = the mean number of
+ * neighbours.  psi (nullable, host, 8*mx*my doubles) receives psi_6(j) of
+ * every slot in the layout of hdmc_get_state (real, imaginary; 0 for unused
+ * slots); asking for it allocates 64 bytes of device memory per cell for
+ * the duration of the call.  0 < r_cut <= 2 min(wx, wy), else HDMC_EINVAL.
+ * Synchronises. */
+int hdmc_psi6(hdmc_t *h, double r_cut, double out[4], double *psi);
+
 /* Global coordinates of every disk into host xy[2N], in canonical (cell,
  * slot) order: x = O_x + cx*wx + local_x wrapped into [0, mx*wx) (likewise
  * y), O the accumulated grid origin; cells use the binary32 widths in

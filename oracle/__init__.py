@@ -70,6 +70,9 @@ def lib():
             "orc_state": (None, [vp, _f64p, _u8p]),
             "orc_positions": (None, [vp, _f64p]),
             "orc_histogram": (None, [vp, ctypes.c_int, ctypes.c_double, _u64p]),
+            "orc_psi6": (None, [vp, ctypes.c_double, _f64p, _f64p]),
+            "orc_bruteforce_psi6": (None, [_f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, _f64p, _f64p]),
             "orc_bruteforce_close_pairs": (ctypes.c_int64, [_f64p, ctypes.c_int64, ctypes.c_double,
                                                             ctypes.c_double, ctypes.c_double]),
             "orc_bruteforce_histogram": (None, [_f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
@@ -166,6 +169,16 @@ def bruteforce_histogram(xy, Lx, Ly, sigma, nbins, dr):
     h = np.zeros(nbins, dtype=np.uint64)
     lib().orc_bruteforce_histogram(_p(xy, _f64p), xy.size // 2, Lx, Ly, sigma, nbins, dr, _p(h, _u64p))
     return h
+
+
+def bruteforce_psi6(xy, Lx, Ly, rcut):
+    """psi_6 sums and per-disk values by brute force over all pairs and the
+    3x3 periodic images of global coordinates."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    out = np.zeros(4, dtype=np.float64)
+    psi = np.zeros(xy.size, dtype=np.float64)
+    lib().orc_bruteforce_psi6(_p(xy, _f64p), xy.size // 2, Lx, Ly, rcut, _p(out, _f64p), _p(psi, _f64p))
+    return out, psi.reshape(-1, 2)
 
 
 def displacements(seed, sweep, Q, t, precision, ncells):
@@ -312,6 +325,18 @@ class System:
         h = np.zeros(nbins, dtype=np.uint64)
         lib().orc_histogram(self._h, nbins, dr * self.sigma, _p(h, _u64p))
         return h
+
+    def psi6(self, rcut=None, per_disk=False):
+        """Sums (re, im, |.|, neighbours) of psi_6 over the disks; with
+        per_disk, also psi_6 of every slot, shape (mx*my, 4, 2)."""
+        rcut = 1.4 * self.sigma if rcut is None else rcut
+        out = np.zeros(4, dtype=np.float64)
+        if per_disk:
+            psi = np.zeros(8 * self.mx * self.my, dtype=np.float64)
+            lib().orc_psi6(self._h, rcut, _p(out, _f64p), _p(psi, _f64p))
+            return out, psi.reshape(-1, 4, 2)
+        lib().orc_psi6(self._h, rcut, _p(out, _f64p), None)
+        return out
 
     def local_overlaps(self):
         return int(lib().orc_local_overlaps(self._h))

@@ -1076,6 +1076,101 @@ void orc_histogram(const oracle_t *o, int nbins, double dr, uint64_t *hist)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Bond-orientational order psi_6 (the "average orientational order           */
+/* parameter" whose autocorrelation time Sec. 3.3 minimises).  Reading: the   */
+/* neighbours k of disk j are the other disks closer than r_cut (given by the */
+/* caller, at most two cell widths); psi_6(j) = (1/n_j) sum_k (z_jk/|z_jk|)^6 */
+/* with z_jk = dx + i dy, the separation in cell-local terms as in the        */
+/* histogram; psi_6(j) = 0 without neighbours.  (z/|z|)^6 = z^6 / (|z|^2)^3:  */
+/* complex products and one division per pair, in the order written.         */
+/* out[0] + i out[1] = sum_j psi_6(j), out[2] = sum_j |psi_6(j)|,             */
+/* out[3] = sum_j n_j; psi (nullable) receives psi_6 of every slot in the     */
+/* canonical layout psi[(4c + j)*2 + k], k = 0 real, 1 imaginary (0 where a   */
+/* slot is unused).                                                            */
+/* ------------------------------------------------------------------------ */
+void orc_psi6(const oracle_t *o, double rcut, double out[4], double *psi)
+{
+    const double wx = o->prec == 0 ? o->wx : (double)o->wxf;
+    const double wy = o->prec == 0 ? o->wy : (double)o->wyf;
+    const double rc2 = rcut * rcut;
+    double sre = 0.0, sim = 0.0, sabs = 0.0, snb = 0.0;
+    if (psi) memset(psi, 0, sizeof(double) * 8 * (size_t)o->mx * (size_t)o->my);
+    for (int cy = 0; cy < o->my; ++cy)
+        for (int cx = 0; cx < o->mx; ++cx) {
+            int64_t c = (int64_t)cy * o->mx + cx;
+            for (int i = 0; i < o->n[c]; ++i) {
+                double px, py;
+                slot_get(o, c, i, &px, &py);
+                double are = 0.0, aim = 0.0;
+                int nb = 0;
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        int ncx = ((cx + dx) % o->mx + o->mx) % o->mx;
+                        int ncy = ((cy + dy) % o->my + o->my) % o->my;
+                        int64_t nc = (int64_t)ncy * o->mx + ncx;
+                        double sx = (double)dx * wx, sy = (double)dy * wy;
+                        for (int j = 0; j < o->n[nc]; ++j) {
+                            if (dx == 0 && dy == 0 && j == i) continue;
+                            double qx, qy;
+                            slot_get(o, nc, j, &qx, &qy);
+                            double ddx = px - (qx + sx), ddy = py - (qy + sy);
+                            double r2 = ddx * ddx + ddy * ddy;
+                            if (!(r2 < rc2)) continue;
+                            double ar = ddx * ddx - ddy * ddy, ai = 2.0 * (ddx * ddy);   /* z^2 */
+                            double br = ar * ddx - ai * ddy, bi = ar * ddy + ai * ddx;   /* z^3 */
+                            double cr = br * br - bi * bi, ci = 2.0 * (br * bi);         /* z^6 */
+                            double r6 = (r2 * r2) * r2;
+                            are += cr / r6;
+                            aim += ci / r6;
+                            nb += 1;
+                        }
+                    }
+                if (nb > 0) {
+                    double pr = are / (double)nb, pi = aim / (double)nb;
+                    sre += pr;
+                    sim += pi;
+                    sabs += sqrt(pr * pr + pi * pi);
+                    if (psi) { psi[(4 * c + i) * 2] = pr; psi[(4 * c + i) * 2 + 1] = pi; }
+                }
+                snb += (double)nb;
+            }
+        }
+    out[0] = sre; out[1] = sim; out[2] = sabs; out[3] = snb;
+}
+
+/* Brute force over all pairs and the 3x3 periodic images (global
+ * coordinates), same definition; psi[2*p + k] per disk p (nullable). */
+void orc_bruteforce_psi6(const double *xy, int64_t N, double Lx, double Ly, double rcut, double out[4], double *psi)
+{
+    const double rc2 = rcut * rcut;
+    double sre = 0.0, sim = 0.0, sabs = 0.0, snb = 0.0;
+    for (int64_t p = 0; p < N; ++p) {
+        double are = 0.0, aim = 0.0;
+        int nb = 0;
+        for (int64_t q = 0; q < N; ++q)
+            for (int iy = -1; iy <= 1; ++iy)
+                for (int ix = -1; ix <= 1; ++ix) {
+                    if (q == p && ix == 0 && iy == 0) continue;
+                    double ddx = xy[2 * p] - (xy[2 * q] + ix * Lx), ddy = xy[2 * p + 1] - (xy[2 * q + 1] + iy * Ly);
+                    double r2 = ddx * ddx + ddy * ddy;
+                    if (!(r2 < rc2)) continue;
+                    double ar = ddx * ddx - ddy * ddy, ai = 2.0 * (ddx * ddy);
+                    double br = ar * ddx - ai * ddy, bi = ar * ddy + ai * ddx;
+                    double cr = br * br - bi * bi, ci = 2.0 * (br * bi);
+                    double r6 = (r2 * r2) * r2;
+                    are += cr / r6;
+                    aim += ci / r6;
+                    nb += 1;
+                }
+        double pr = 0.0, pi = 0.0;
+        if (nb > 0) { pr = are / (double)nb; pi = aim / (double)nb; }
+        sre += pr; sim += pi; sabs += sqrt(pr * pr + pi * pi); snb += (double)nb;
+        if (psi) { psi[2 * p] = pr; psi[2 * p + 1] = pi; }
+    }
+    out[0] = sre; out[1] = sim; out[2] = sabs; out[3] = snb;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Brute-force checks on global coordinates (tests)                          */
 /* ------------------------------------------------------------------------ */
 static double min_image(double d, double L)

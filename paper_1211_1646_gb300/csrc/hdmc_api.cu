@@ -399,6 +399,39 @@ int hdmc_pressure(hdmc_t* h, double* betaP_over_rho, double* g_contact, uint64_t
     return HDMC_OK;
 }
 
+int hdmc_psi6(hdmc_t* h, double r_cut, double out[4], double* psi) {
+    if (!h || !out) return HDMC_EINVAL;
+    const double wmin = h->prec == HDMC_FP64 ? std::min(h->g.wx, h->g.wy)
+                                             : std::min((double)h->g.wxf, (double)h->g.wyf);
+    if (!(r_cut > 0.0) || !(r_cut <= 2.0 * wmin)) return HDMC_EINVAL;
+    const unsigned nb = psi6_blocks(h->g);
+    // block sums go to the idle half of the double buffer (scratch between sweeps)
+    if (sizeof(double) * 4 * (size_t)nb > h->lay.cells) return HDMC_EINVAL;
+    double* partial = reinterpret_cast<double*>(h->cells[h->cur ^ 1]);
+    const size_t psi_bytes = sizeof(double) * 8 * (size_t)h->g.C;
+    double* dpsi = nullptr;
+    int e = psi ? cuda_code(cudaMalloc((void**)&dpsi, psi_bytes)) : HDMC_OK;
+    if (e) return e;
+    const LaunchCtx c = h->ctx(h->stream);
+    const double rc2 = r_cut * r_cut;
+    if (h->prec == HDMC_FP64) launch_psi6_f64(c, h->cells[h->cur], rc2, dpsi, partial);
+    else launch_psi6_f32(c, h->cells[h->cur], rc2, dpsi, partial);
+    e = cuda_code(cudaGetLastError());
+    std::vector<double> part(4 * (size_t)nb);
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(part.data(), partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                                      h->stream));
+    if (!e && psi) e = cuda_code(cudaMemcpyAsync(psi, dpsi, psi_bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (!e) e = cuda_code(cudaStreamSynchronize(h->stream));
+    if (dpsi) cudaFree(dpsi);
+    if (e) return e;
+    double sum[4] = {0, 0, 0, 0};
+    for (unsigned b = 0; b < nb; ++b)
+        for (int k = 0; k < 4; ++k) sum[k] += part[4 * (size_t)b + k];
+    for (int k = 0; k < 4; ++k) out[k] = sum[k] / (double)h->N;
+    return check_device(h);
+}
+
 int hdmc_positions(hdmc_t* h, double* xy, int32_t* cell) {
     if (!h || !xy) return HDMC_EINVAL;
     HostState hs;

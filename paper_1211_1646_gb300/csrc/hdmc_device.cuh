@@ -238,6 +238,7 @@ dim3 subsweep_grid(const Geometry& g);
 void launch_subsweep_f64(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k);
 void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw);
 void launch_hist_f64(const LaunchCtx& c, const void* cells);
+void launch_psi6_f64(const LaunchCtx& c, const void* cells, double rc2, double* psi, double* partial);
 void launch_check_f64(const LaunchCtx& c, const void* cells, unsigned long long* out);
 
 void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw, int k);
@@ -264,6 +265,8 @@ void launch_shift_batch(const BatchCtx& c, int prec, const void* src, void* dst,
 void launch_hist_batch(const BatchCtx& c, int prec, const void* arena);
 void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw);
 void launch_hist_f32(const LaunchCtx& c, const void* cells);
+void launch_psi6_f32(const LaunchCtx& c, const void* cells, double rc2, double* psi, double* partial);
+unsigned psi6_blocks(const Geometry& g);   // blocks of one psi_6 launch
 void launch_check_f32(const LaunchCtx& c, const void* cells, unsigned long long* out);
 
 }  // namespace hdmc

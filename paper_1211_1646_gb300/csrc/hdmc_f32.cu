@@ -15,6 +15,13 @@ void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const Swee
     launch_shift_t<float>(c, src, dst, draw);
 }
 void launch_hist_f32(const LaunchCtx& c, const void* cells) { launch_hist_t<float>(c, cells); }
+void launch_psi6_f32(const LaunchCtx& c, const void* cells, double rc2, double* psi, double* partial) {
+    launch_psi6_t<float>(c, cells, rc2, psi, partial);
+}
+unsigned psi6_blocks(const Geometry& g) {
+    const dim3 grid = set_grid(g, dim3(kHistBX, kHistBY));
+    return grid.x * grid.y * grid.z;
+}
 void launch_check_f32(const LaunchCtx& c, const void* cells, unsigned long long* out) {
     launch_check_t<float>(c, cells, out);
 }

@@ -10,6 +10,9 @@ void launch_shift_f64(const LaunchCtx& c, const void* src, void* dst, const Swee
     launch_shift_t<double>(c, src, dst, draw);
 }
 void launch_hist_f64(const LaunchCtx& c, const void* cells) { launch_hist_t<double>(c, cells); }
+void launch_psi6_f64(const LaunchCtx& c, const void* cells, double rc2, double* psi, double* partial) {
+    launch_psi6_t<double>(c, cells, rc2, psi, partial);
+}
 void launch_check_f64(const LaunchCtx& c, const void* cells, unsigned long long* out) {
     launch_check_t<double>(c, cells, out);
 }

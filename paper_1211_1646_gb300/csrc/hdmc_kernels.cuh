@@ -254,6 +254,96 @@ k_hist(const Geometry g, const T* __restrict__ cells, const double* __restrict__
     hist_cells<T>(g, cells, edges2, hist, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// ---- bond-orientational order psi_6 (Sec. 3.3's order parameter) -------------------------
+// Neighbours k of disk j: the other disks closer than r_cut (r_cut <= 2 w, so
+// the 5x5 neighbourhood holds them); psi_6(j) = (1/n_j) sum_k z^6 / (|z|^2)^3,
+// z = dx + i dy from cell-local coordinates as in the histogram, 0 without
+// neighbours.  Pairs in the order dy, dx, slot and every binary64 operation
+// explicitly rounded, so psi_6(j) is the same number whatever the launch.
+// One thread per cell (grid of the histogram); block sums of
+// {re, im, |psi_6|, n} in a fixed order to partial[4 * block].
+template <typename T>
+__global__ void __launch_bounds__(kHistBX * kHistBY)
+k_psi6(const Geometry g, const T* __restrict__ cells, double rc2, double* __restrict__ psi,
+       double* __restrict__ partial) {
+    __shared__ double red[kHistBY][4];
+    const int q = blockIdx.z;
+    const int hx = blockIdx.x * kHistBX + threadIdx.x, hy = blockIdx.y * kHistBY + threadIdx.y;
+    const bool live = hx < g.hx && hy < g.hy;
+    const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
+    const double wxd = (double)Prm<T>::wx(g), wyd = (double)Prm<T>::wy(g);
+    Cell<T> own;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = T(kEmpty);
+    if (live) load_cell_ro(cells + 8 * ((long long)q * g.cq + (long long)hy * g.hx + hx), own);
+    double are[4] = {0, 0, 0, 0}, aim[4] = {0, 0, 0, 0};
+    int nb[4] = {0, 0, 0, 0};
+    if (live) {
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                Cell<T> c;
+                load_cell_ro(cells + 8 * storage_index(g, wrap(cx + dx, g.mx), wrap(cy + dy, g.my)), c);
+                const double sx = (double)dx * wxd, sy = (double)dy * wyd;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (!Prm<T>::ge0(own.x[i])) continue;
+                    const double px = (double)own.x[i], py = (double)own.y[i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!Prm<T>::ge0(c.x[j]) || (dx == 0 && dy == 0 && j == i)) continue;
+                        const double ddx = __dsub_rn(px, __dadd_rn((double)c.x[j], sx));
+                        const double ddy = __dsub_rn(py, __dadd_rn((double)c.y[j], sy));
+                        const double r2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+                        if (!(r2 < rc2)) continue;
+                        const double ar = __dsub_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));   // z^2
+                        const double ai = __dmul_rn(2.0, __dmul_rn(ddx, ddy));
+                        const double br = __dsub_rn(__dmul_rn(ar, ddx), __dmul_rn(ai, ddy));     // z^3
+                        const double bi = __dadd_rn(__dmul_rn(ar, ddy), __dmul_rn(ai, ddx));
+                        const double zr = __dsub_rn(__dmul_rn(br, br), __dmul_rn(bi, bi));      // z^6
+                        const double zi = __dmul_rn(2.0, __dmul_rn(br, bi));
+                        const double r6 = __dmul_rn(__dmul_rn(r2, r2), r2);
+                        are[i] = __dadd_rn(are[i], __ddiv_rn(zr, r6));
+                        aim[i] = __dadd_rn(aim[i], __ddiv_rn(zi, r6));
+                        nb[i] += 1;
+                    }
+                }
+            }
+    }
+    double t[4] = {0, 0, 0, 0};   // re, im, |psi_6|, neighbours of this thread's disks
+    const long long cc = (long long)cy * g.mx + cx;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!live || !Prm<T>::ge0(own.x[i])) continue;
+        double pr = 0.0, pi = 0.0;
+        if (nb[i] > 0) {
+            pr = __ddiv_rn(are[i], (double)nb[i]);
+            pi = __ddiv_rn(aim[i], (double)nb[i]);
+            t[0] = __dadd_rn(t[0], pr);
+            t[1] = __dadd_rn(t[1], pi);
+            t[2] = __dadd_rn(t[2], __dsqrt_rn(__dadd_rn(__dmul_rn(pr, pr), __dmul_rn(pi, pi))));
+        }
+        t[3] = __dadd_rn(t[3], (double)nb[i]);
+        if (psi) {
+            psi[(4 * cc + i) * 2] = pr;
+            psi[(4 * cc + i) * 2 + 1] = pi;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o > 0; o >>= 1) t[k] = __dadd_rn(t[k], __shfl_down_sync(0xffffffffu, t[k], o));
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) red[threadIdx.y][k] = t[k];
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        for (int k = 0; k < 4; ++k) {
+            double v = 0.0;
+            for (int w = 0; w < kHistBY; ++w) v = __dadd_rn(v, red[w][k]);
+            partial[4 * b + k] = v;
+        }
+    }
+}
+
 // ---- batched replicas ------------------------------------------------------------------
 // Every stage is one launch over all replicas of a batch: the launch's flat
 // block index is mapped to (replica, local block) by a per-stage table, and
@@ -324,6 +414,13 @@ void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepD
     const dim3 block(kShiftBX, kShiftBY);
     launch_on(c, k_shift<T>, set_grid(c.g, block), block, c.g, reinterpret_cast<const T*>(src),
               reinterpret_cast<T*>(dst), draw, c.st);
+}
+
+template <typename T>
+void launch_psi6_t(const LaunchCtx& c, const void* cells, double rc2, double* psi, double* partial) {
+    const dim3 block(kHistBX, kHistBY);
+    k_psi6<T><<<set_grid(c.g, block), block, 0, c.stream>>>(c.g, reinterpret_cast<const T*>(cells), rc2, psi,
+                                                             partial);
 }
 
 template <typename T>

@@ -42,6 +42,7 @@ SIGNATURES = {
     "hdmc_sample": (ctypes.c_int, [_vp]),
     "hdmc_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
     "hdmc_positions": (ctypes.c_int, [_vp, _f64p, _i32p]),
+    "hdmc_psi6": (ctypes.c_int, [_vp, ctypes.c_double, _f64p, _f64p]),
     "hdmc_get_state": (ctypes.c_int, [_vp, _f64p, _u8p]),
     "hdmc_set_state": (ctypes.c_int, [_vp, _f64p, _u8p, _f64p, ctypes.c_uint64, ctypes.c_uint64]),
     "hdmc_snapshot_bytes": (ctypes.c_size_t, [_vp]),
@@ -171,6 +172,18 @@ def hdmc_positions(h, N):
     cell = np.zeros(N, dtype=np.int32)
     _check(lib().hdmc_positions(h, _p(xy, _f64p), _p(cell, _i32p)), "hdmc_positions")
     return xy.reshape(N, 2), cell
+
+
+def hdmc_psi6(h, r_cut, C=None):
+    """(mean psi_6 as a complex number, mean |psi_6|, mean neighbours), and
+    psi_6 of every slot, shape (C, 4, 2), when C (cells) is given."""
+    out = np.zeros(4, dtype=np.float64)
+    if C is None:
+        _check(lib().hdmc_psi6(h, r_cut, _p(out, _f64p), None), "hdmc_psi6")
+        return complex(out[0], out[1]), out[2], out[3]
+    psi = np.zeros(8 * C, dtype=np.float64)
+    _check(lib().hdmc_psi6(h, r_cut, _p(out, _f64p), _p(psi, _f64p)), "hdmc_psi6")
+    return complex(out[0], out[1]), out[2], out[3], psi.reshape(C, 4, 2)
 
 
 def hdmc_get_state(h, C):
@@ -443,6 +456,11 @@ class System:
 
     def counters(self):
         return hdmc_counters(self.h)
+
+    def psi6(self, r_cut=1.4, per_disk=False):
+        """Orientational order: (mean psi_6, mean |psi_6|, mean neighbours
+        [, psi_6 per slot]); r_cut in the units of the box."""
+        return hdmc_psi6(self.h, r_cut, self.C if per_disk else None)
 
     def snapshot_bytes(self):
         return hdmc_snapshot_bytes(self.h)
