@@ -277,6 +277,25 @@ int hdmc_batch_pressure(hdmc_batch_t *b, double *betaP_over_rho, double *g_conta
 /* Raw state of replica r in the layout of hdmc_get_state.  Synchronises. */
 int hdmc_batch_get_state(hdmc_batch_t *b, int r, double *local, uint8_t *counts);
 
+/* Batch snapshots, as hdmc_save / hdmc_load for every replica at once: a
+ * 256-byte header (magic "HDMCBSN1", version, precision, R, sub-sweep
+ * block height, sweeps, sample count), then at 256-byte aligned offsets one
+ * record per replica (N, box, sigma, d, n_M, grid, seed, balance controls),
+ * the replicas' device state words, their trial counter totals, their
+ * histogram accumulators and the arena of cells.  Loading requires the same
+ * replicas (N, box, sigma, grid) and precision; d, n_M, seeds, controls and
+ * the block height come from the image.  The cells are checked on the
+ * device, replica by replica, before anything is replaced; a bad image is
+ * rejected with HDMC_EINVAL and the batch keeps its state.  Both
+ * synchronise. */
+size_t hdmc_batch_snapshot_bytes(const hdmc_batch_t *b);
+int hdmc_batch_save(hdmc_batch_t *b, void *buf, size_t bytes);
+int hdmc_batch_load(hdmc_batch_t *b, const void *buf, size_t bytes);
+
+/* psi_6 of every replica, as hdmc_psi6 (no per-slot output): out[4r + k].
+ * r_cut must suit every replica's cells.  Synchronises. */
+int hdmc_batch_psi6(hdmc_batch_t *b, double r_cut, double *out);
+
 /* Per-replica trial counters out[4r + k], k as in hdmc_counters.  Synchronises. */
 int hdmc_batch_counters(hdmc_batch_t *b, uint64_t *out);
 

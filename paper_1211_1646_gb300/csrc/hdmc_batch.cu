@@ -559,6 +559,234 @@ int hdmc_batch_autotune(hdmc_batch_t* b, int64_t sweeps, int32_t* rows_per_block
     return check_batch(b);
 }
 
+int hdmc_batch_psi6(hdmc_batch_t* b, double r_cut, double* out) {
+    if (!b || !out || !(r_cut > 0.0)) return HDMC_EINVAL;
+    for (int r = 0; r < b->R; ++r) {
+        const Geometry& g = b->sys[r].g;
+        const double wmin = b->prec == HDMC_FP64 ? std::min(g.wx, g.wy) : std::min((double)g.wxf, (double)g.wyf);
+        if (!(r_cut <= 2.0 * wmin)) return HDMC_EINVAL;
+    }
+    // one launch per replica on its slice of the arena; block sums in the
+    // idle half of the double buffer (scratch between sweeps)
+    const cudaStream_t s = b->stream;
+    const size_t el = b->prec == HDMC_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<size_t> off(b->R + 1, 0);
+    for (int r = 0; r < b->R; ++r) off[r + 1] = off[r] + 4 * (size_t)psi6_blocks(b->sys[r].g);
+    if (sizeof(double) * off[b->R] > b->lay.arena) return HDMC_EINVAL;
+    double* partial = reinterpret_cast<double*>(b->arena[b->cur ^ 1]);
+    const char* cur = static_cast<const char*>(b->arena[b->cur]);
+    int e = HDMC_OK;
+    for (int r = 0; r < b->R && !e; ++r) {
+        LaunchCtx c;
+        c.g = b->sys[r].g;
+        c.stream = s;
+        const void* cells = cur + (size_t)b->cell_off[r] * 8 * el;
+        if (b->prec == HDMC_FP64) launch_psi6_f64(c, cells, r_cut * r_cut, nullptr, partial + off[r]);
+        else launch_psi6_f32(c, cells, r_cut * r_cut, nullptr, partial + off[r]);
+        e = cuda_code(cudaGetLastError());
+    }
+    std::vector<double> part(off[b->R]);
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(part.data(), partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    for (int r = 0; r < b->R; ++r) {
+        double sum[4] = {0, 0, 0, 0};
+        for (size_t i = off[r]; i < off[r + 1]; i += 4)
+            for (int k = 0; k < 4; ++k) sum[k] += part[i + k];
+        for (int k = 0; k < 4; ++k) out[4 * r + k] = sum[k] / (double)b->sys[r].N;
+    }
+    return HDMC_OK;
+}
+
+// ---- batch snapshots ------------------------------------------------------------------
+namespace {
+
+constexpr char kBatchMagic[8] = {'H', 'D', 'M', 'C', 'B', 'S', 'N', '1'};
+constexpr uint32_t kBatchVersion = 1;
+constexpr size_t kBatchHeader = 256;
+
+struct BatchSnapHeader {
+    char magic[8];
+    uint32_t version, precision;
+    int32_t R, rows;
+    uint64_t sweeps;
+    int64_t n_samples;
+    uint64_t off_reps, off_states, off_counters, off_hist, off_cells, cell_bytes, total;
+};
+static_assert(sizeof(BatchSnapHeader) <= kBatchHeader, "batch snapshot header");
+
+struct BatchSnapReplica {
+    int64_t N;
+    double Lx, Ly, sigma, d;
+    int32_t nsel, mx, my, pad0;
+    uint32_t key0, key1, flags, pad1;
+};
+
+struct BatchSnapLayout {
+    size_t reps, states, counters, hist, cells, cell_bytes, total;
+};
+
+BatchSnapLayout batch_snap_layout(const hdmc_batch_t* b) {
+    BatchSnapLayout L;
+    size_t p = kBatchHeader;
+    L.reps = p;
+    p += align_up(sizeof(BatchSnapReplica) * (size_t)b->R);
+    L.states = p;
+    p += align_up(sizeof(DevState) * (size_t)b->R);
+    L.counters = p;
+    p += align_up(sizeof(unsigned long long) * 4 * (size_t)b->R);
+    L.hist = p;
+    p += align_up(sizeof(unsigned long long) * kHistBins * (size_t)b->R);
+    L.cells = p;
+    L.cell_bytes = (size_t)b->lay.cells * 8 * (b->prec == HDMC_FP64 ? sizeof(double) : sizeof(float));
+    L.total = p + L.cell_bytes;
+    return L;
+}
+
+}  // namespace
+
+size_t hdmc_batch_snapshot_bytes(const hdmc_batch_t* b) { return b ? batch_snap_layout(b).total : 0; }
+
+int hdmc_batch_save(hdmc_batch_t* b, void* buf, size_t bytes) {
+    if (!b || !buf) return HDMC_EINVAL;
+    const BatchSnapLayout L = batch_snap_layout(b);
+    if (bytes < L.total) return HDMC_EINVAL;
+    char* p = static_cast<char*>(buf);
+    std::vector<unsigned long long> tot;
+    int e = read_counters(b, tot);   // synchronises
+    if (e) return e;
+    std::memset(p, 0, L.cells);
+    BatchSnapHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kBatchMagic, sizeof(kBatchMagic));
+    hd.version = kBatchVersion;
+    hd.precision = (uint32_t)b->prec;
+    hd.R = b->R;
+    hd.rows = b->rows;
+    hd.sweeps = b->sweeps;
+    hd.n_samples = b->n_samples;
+    hd.off_reps = L.reps;
+    hd.off_states = L.states;
+    hd.off_counters = L.counters;
+    hd.off_hist = L.hist;
+    hd.off_cells = L.cells;
+    hd.cell_bytes = L.cell_bytes;
+    hd.total = L.total;
+    std::memcpy(p, &hd, sizeof(hd));
+    for (int r = 0; r < b->R; ++r) {
+        const SysDesc& d = b->sys[r];
+        BatchSnapReplica rec;
+        std::memset(&rec, 0, sizeof(rec));
+        rec.N = d.N;
+        rec.Lx = d.Lx;
+        rec.Ly = d.Ly;
+        rec.sigma = d.g.sigma;
+        rec.d = d.g.d;
+        rec.nsel = d.g.nsel;
+        rec.mx = d.g.mx;
+        rec.my = d.g.my;
+        rec.key0 = d.g.key0;
+        rec.key1 = d.g.key1;
+        rec.flags = d.g.flags;
+        std::memcpy(p + L.reps + sizeof(rec) * (size_t)r, &rec, sizeof(rec));
+    }
+    std::memcpy(p + L.counters, tot.data(), sizeof(unsigned long long) * tot.size());
+    const cudaStream_t s = b->stream;
+    e = cuda_code(cudaMemcpyAsync(p + L.states, b->sts, sizeof(DevState) * (size_t)b->R, cudaMemcpyDeviceToHost, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(p + L.hist, b->hist, sizeof(unsigned long long) * kHistBins * (size_t)b->R,
+                                      cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaMemcpyAsync(p + L.cells, b->arena[b->cur], L.cell_bytes, cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    for (int r = 0; r < b->R; ++r) {
+        DevState ds;
+        std::memcpy(&ds, p + L.states + sizeof(DevState) * (size_t)r, sizeof(ds));
+        if (ds.error & 1u) return HDMC_EOVERFLOW;
+    }
+    return HDMC_OK;
+}
+
+int hdmc_batch_load(hdmc_batch_t* b, const void* buf, size_t bytes) {
+    if (!b || !buf) return HDMC_EINVAL;
+    const BatchSnapLayout L = batch_snap_layout(b);
+    if (bytes < L.total) return HDMC_EINVAL;
+    const char* p = static_cast<const char*>(buf);
+    BatchSnapHeader hd;
+    std::memcpy(&hd, p, sizeof(hd));
+    if (std::memcmp(hd.magic, kBatchMagic, sizeof(kBatchMagic)) != 0 || hd.version != kBatchVersion ||
+        hd.precision != (uint32_t)b->prec || hd.R != b->R || hd.n_samples < 0 || hd.off_reps != L.reps ||
+        hd.off_states != L.states || hd.off_counters != L.counters || hd.off_hist != L.hist ||
+        hd.off_cells != L.cells || hd.cell_bytes != L.cell_bytes || hd.total != L.total)
+        return HDMC_EINVAL;
+    std::vector<BatchSnapReplica> recs(b->R);
+    for (int r = 0; r < b->R; ++r) {
+        BatchSnapReplica& rec = recs[r];
+        std::memcpy(&rec, p + L.reps + sizeof(rec) * (size_t)r, sizeof(rec));
+        const SysDesc& d = b->sys[r];
+        if (rec.N != d.N || rec.Lx != d.Lx || rec.Ly != d.Ly || rec.sigma != d.g.sigma || rec.mx != d.g.mx ||
+            rec.my != d.g.my || rec.nsel < 1 || rec.nsel > 255 || !(rec.d > 0) || !(rec.d < 0.5 * d.g.wx) ||
+            !(rec.d < 0.5 * d.g.wy) || (rec.flags & ~(kNoParticleShuffle | kNoSetShuffle)) != 0)
+            return HDMC_EINVAL;
+        DevState ds;
+        std::memcpy(&ds, p + L.states + sizeof(DevState) * (size_t)r, sizeof(ds));
+        if (ds.error != 0 || !std::isfinite(ds.origin[0]) || !std::isfinite(ds.origin[1])) return HDMC_EINVAL;
+    }
+    // cells into the idle half of the double buffer, checked there replica by
+    // replica (results in the draw table, scratch until the next sweep)
+    const cudaStream_t s = b->stream;
+    const size_t el = b->prec == HDMC_FP64 ? sizeof(double) : sizeof(float);
+    char* idle = static_cast<char*>(b->arena[b->cur ^ 1]);
+    unsigned long long* res = reinterpret_cast<unsigned long long*>(b->table);
+    int e = cuda_code(cudaStreamSynchronize(s));
+    if (!e) e = cuda_code(cudaMemsetAsync(res, 0, sizeof(unsigned long long) * 2 * (size_t)b->R, s));
+    if (!e) e = cuda_code(cudaMemcpyAsync(idle, p + L.cells, L.cell_bytes, cudaMemcpyHostToDevice, s));
+    for (int r = 0; r < b->R && !e; ++r) {
+        LaunchCtx c;
+        c.g = b->sys[r].g;
+        c.stream = s;
+        void* cells = idle + (size_t)b->cell_off[r] * 8 * el;
+        if (b->prec == HDMC_FP64) launch_check_f64(c, cells, res + 2 * r);
+        else launch_check_f32(c, cells, res + 2 * r);
+        e = cuda_code(cudaGetLastError());
+    }
+    std::vector<unsigned long long> got(2 * (size_t)b->R);
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(got.data(), res, sizeof(unsigned long long) * got.size(), cudaMemcpyDeviceToHost,
+                                      s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    for (int r = 0; r < b->R; ++r)
+        if (got[2 * r + 1] != 0 || got[2 * r] != (unsigned long long)b->sys[r].N) return HDMC_EINVAL;
+    // commit
+    e = cuda_code(cudaMemcpyAsync(b->sts, p + L.states, sizeof(DevState) * (size_t)b->R, cudaMemcpyHostToDevice, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(b->hist, p + L.hist, sizeof(unsigned long long) * kHistBins * (size_t)b->R,
+                                      cudaMemcpyHostToDevice, s));
+    if (!e) e = cuda_code(cudaMemsetAsync(b->partial, 0, b->lay.partial, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    b->counter_base.assign(4 * (size_t)b->R, 0);
+    std::memcpy(b->counter_base.data(), p + L.counters, sizeof(unsigned long long) * 4 * (size_t)b->R);
+    for (int r = 0; r < b->R; ++r) {
+        Geometry& g = b->sys[r].g;
+        g.d = recs[r].d;
+        g.df = (float)recs[r].d;
+        g.nsel = recs[r].nsel;
+        g.key0 = recs[r].key0;
+        g.key1 = recs[r].key1;
+        g.flags = recs[r].flags;
+    }
+    b->cur ^= 1;
+    b->sweeps = hd.sweeps;
+    b->n_samples = hd.n_samples;
+    b->drop_graphs();
+    const int rows = (b->prec == HDMC_FP32_LOCAL &&
+                      (hd.rows == 1 || hd.rows == 2 || hd.rows == 4 || hd.rows == 8)) ? hd.rows : b->rows;
+    return upload_layout(b, rows);
+}
+
 void hdmc_batch_destroy(hdmc_batch_t* b) {
     if (!b) return;
     if (b->stream || b->ws) cudaStreamSynchronize(b->stream);

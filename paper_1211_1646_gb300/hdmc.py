@@ -67,6 +67,10 @@ SIGNATURES = {
     "hdmc_batch_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
     "hdmc_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _u8p]),
     "hdmc_batch_counters": (ctypes.c_int, [_vp, _u64p]),
+    "hdmc_batch_psi6": (ctypes.c_int, [_vp, ctypes.c_double, _f64p]),
+    "hdmc_batch_snapshot_bytes": (ctypes.c_size_t, [_vp]),
+    "hdmc_batch_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "hdmc_batch_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hdmc_batch_info": (ctypes.c_int, [_vp, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _u64p, _f64p]),
     "hdmc_batch_set_nselect": (ctypes.c_int, [_vp, _i32p]),
     "hdmc_batch_set_rows": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -359,6 +363,28 @@ def hdmc_batch_set_nselect(b, nselect):
     _check(lib().hdmc_batch_set_nselect(b, _p(ns, _i32p)), "hdmc_batch_set_nselect")
 
 
+def hdmc_batch_psi6(b, r_cut, R):
+    out = np.zeros(4 * R, dtype=np.float64)
+    _check(lib().hdmc_batch_psi6(b, r_cut, _p(out, _f64p)), "hdmc_batch_psi6")
+    out = out.reshape(R, 4)
+    return out[:, 0] + 1j * out[:, 1], out[:, 2], out[:, 3]
+
+
+def hdmc_batch_snapshot_bytes(b):
+    return int(lib().hdmc_batch_snapshot_bytes(b))
+
+
+def hdmc_batch_save(b, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc_batch_save(b, ptr, n), "hdmc_batch_save")
+    return buf
+
+
+def hdmc_batch_load(b, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc_batch_load(b, ptr, n), "hdmc_batch_load")
+
+
 def hdmc_batch_set_rows(b, rows):
     _check(lib().hdmc_batch_set_rows(b, rows), "hdmc_batch_set_rows")
 
@@ -561,6 +587,23 @@ class Batch:
 
     def set_rows(self, rows):
         hdmc_batch_set_rows(self.b, rows)
+
+    def snapshot_bytes(self):
+        return hdmc_batch_snapshot_bytes(self.b)
+
+    def psi6(self, r_cut=1.4):
+        """Per replica: mean psi_6 (complex), mean |psi_6|, mean neighbours."""
+        return hdmc_batch_psi6(self.b, r_cut, self.R)
+
+    def save(self, buf=None):
+        """Snapshot of every replica into buf (numpy uint8 array or host
+        tensor); a new numpy array when buf is None."""
+        if buf is None:
+            buf = np.empty(self.snapshot_bytes(), dtype=np.uint8)
+        return hdmc_batch_save(self.b, buf)
+
+    def load(self, buf):
+        hdmc_batch_load(self.b, buf)
 
     def set_balance(self, shuffle_particles, shuffle_sets):
         """Per-replica Table 1 negative controls (sequences of R booleans)."""

@@ -134,3 +134,86 @@ def test_batch_of_64_replicas_runs():
     assert np.all(np.isfinite(bp)) and np.all(bp > 1.0)
     cnt = b.counters()
     assert np.all(cnt[:, 0] > 0)
+
+
+def _same_batches(a, b, R):
+    ca, cb = a.counters(), b.counters()
+    for r in range(R):
+        assert np.array_equal(a.state(r)[0], b.state(r)[0]), r
+        assert np.array_equal(a.state(r)[1], b.state(r)[1]), r
+        assert np.array_equal(ca[r], cb[r]), r
+        assert np.array_equal(a.origin(r), b.origin(r)), r
+
+
+def test_batch_snapshot_resume_is_bit_identical():
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    a = hdmc.Batch(reps, precision="fp32")
+    a.sweep(30)
+    a.set_rows(2)
+    a.set_nselect([3, 5, 2, 4])
+    a.set_balance([True, False, True, True], [True, True, False, True])
+    a.sweep(10)
+    a.sample()
+    img = a.save()
+    assert img.nbytes == a.snapshot_bytes()
+    # a batch of the same replicas with other seeds, d and n_M takes them from the image
+    other = [W.Workload(w.name, w.N, w.Lx, w.Ly, 0.05, 1, w.seed + 1000, 0) for w in reps]
+    b = hdmc.Batch(other, precision="fp32")
+    b.sweep(3)
+    b.load(img)
+    assert b.config()[0] == 2 and list(b.config()[1]) == [3, 5, 2, 4]
+    _same_batches(a, b, len(reps))
+    for x in (a, b):
+        x.sweep(70)
+        x.sample()
+    _same_batches(a, b, len(reps))
+    pa, pb = a.pressure(), b.pressure()
+    assert pa[3] == pb[3] == 2
+    assert np.array_equal(pa[2], pb[2]) and np.array_equal(pa[0], pb[0])
+
+
+def test_batch_snapshot_rejects_bad_images_and_keeps_state():
+    import struct
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    src = hdmc.Batch(reps, precision="fp32")
+    src.sweep(12)
+    good = src.save()
+    dst = hdmc.Batch(reps, precision="fp32")
+    ref = hdmc.Batch(reps, precision="fp32")
+    dst.sweep(5)
+    ref.sweep(5)
+    off_cells = struct.unpack_from("<Q", bytes(good[72:80]))[0]   # header field off_cells
+    bad = good.copy()
+    cells = bad[off_cells:].view(np.float32)
+    first = int(np.argmax(cells >= 0))          # an occupied x coordinate
+    cells[first] = 1e6                          # far outside its cell
+    with pytest.raises(hdmc.HDMCError) as e:
+        dst.load(bad)
+    assert e.value.code == hdmc.HDMC_EINVAL
+    short = good[:-1]
+    with pytest.raises(hdmc.HDMCError):
+        dst.load(short)
+    three = hdmc.Batch(reps[:3], precision="fp32")
+    with pytest.raises(hdmc.HDMCError):
+        three.load(np.resize(good, three.snapshot_bytes()))
+    _same_batches(dst, ref, len(reps))
+    dst.sweep(7)
+    ref.sweep(7)
+    _same_batches(dst, ref, len(reps))
+    dst.load(good)
+    _same_batches(dst, src, len(reps))
+
+
+def test_batch_psi6_equals_single_systems():
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision="fp32")
+    singles = _singles(reps, "fp32")
+    b.sweep(25)
+    for s in singles:
+        s.sweep(25)
+    mean, mabs, mnb = b.psi6(1.4)
+    for r, s in enumerate(singles):
+        assert (mean[r], mabs[r], mnb[r]) == s.psi6(1.4)

@@ -100,6 +100,41 @@ def test_n4m_phi0716_fp32():
     _same(g, r)
 
 
+def test_n4m_phi0716_fp64():
+    w = W.n4m(0.716, "fp64")
+    g, r = _pair(w, "fp64")
+    g.sweep(2)
+    r.sweep(2)
+    _same(g, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["wide", "tall", "d_max", "dilute", "dense"])
+def test_geometry_and_density_extremes(prec, case):
+    """Elongated boxes (shift and wrap along a long and a short axis), the
+    largest legal move (just under half a cell), a dilute system (most cells
+    empty) and one near close packing."""
+    if case in ("wide", "tall"):
+        nx, ny = (200, 8) if case == "wide" else (8, 200)
+        Lx, Ly = W.hex_box(nx, ny, 0.70)
+        w = W.Workload(case, nx * ny, Lx, Ly, 0.12, 4, 31, 0)
+    elif case == "d_max":
+        Lx, Ly = W.square_box(1024, 0.60)
+        mx = 2 * int(Lx / 2)
+        w = W.Workload(case, 1024, Lx, Ly, 0.499 * Lx / mx, 4, 32, 0)
+    else:
+        phi = 0.20 if case == "dilute" else 0.85
+        nx, ny = W.hex_counts(4096)
+        Lx, Ly = W.hex_box(nx, ny, phi)
+        w = W.Workload(case, nx * ny, Lx, Ly, 0.15 if case == "dilute" else 0.02, 4, 33, 0)
+    g, r = _pair(w, prec)
+    g.sweep(70)
+    r.sweep(70)
+    _same(g, r, case)
+    c = g.counters()
+    assert c[0] == c[1] + c[2] + c[3] and c[1] > 0
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ragged_grid_and_nselect(prec):
     # 36 x 22 cells: set rows of 18 cells (not a multiple of 32), 11 set rows
