@@ -89,6 +89,32 @@ def lib():
             "orc_visit_sequence": (None, [ctypes.c_int, ctypes.c_int, _i32p]),
             "orc_local_overlaps": (ctypes.c_int, [vp]),
             "orc_edges2": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _f64p]),
+            # three dimensions
+            "orc3_decode_perm": (None, [ctypes.c_int, ctypes.c_uint32, _i32p]),
+            "orc3_grid": (ctypes.c_int, [_f64p, ctypes.c_double, _i32p, _f64p]),
+            "orc3_lattice_positions": (ctypes.c_int, [ctypes.c_int64, _f64p, ctypes.c_double, ctypes.c_uint64,
+                                                      _f64p]),
+            "orc3_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int64, _f64p, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _f64p]),
+            "orc3_destroy": (None, [vp]),
+            "orc3_set_move_size": (ctypes.c_int, [vp, ctypes.c_double]),
+            "orc3_set_balance": (None, [vp, ctypes.c_int, ctypes.c_int]),
+            "orc3_sweep_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, _f64p, _i32p, _i32p, _f64p]),
+            "orc3_cell_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _f64p]),
+            "orc3_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
+            "orc3_shift": (ctypes.c_int, [vp]),
+            "orc3_subsweep": (None, [vp, ctypes.c_uint32, ctypes.c_int]),
+            "orc3_info": (None, [vp, _i32p, _f64p, _u64p, _u64p]),
+            "orc3_counters": (None, [vp, _u64p]),
+            "orc3_origin": (None, [vp, _f64p]),
+            "orc3_state": (None, [vp, _f64p, _u8p]),
+            "orc3_positions": (None, [vp, _f64p]),
+            "orc3_histogram": (None, [vp, ctypes.c_int, ctypes.c_double, _u64p]),
+            "orc3_local_overlaps": (ctypes.c_int, [vp]),
+            "orc3_bruteforce_close_pairs": (ctypes.c_int64, [_f64p, ctypes.c_int64, _f64p, ctypes.c_double]),
+            "orc3_bruteforce_histogram": (None, [_f64p, ctypes.c_int64, _f64p, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_double, _u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -340,3 +366,153 @@ class System:
 
     def local_overlaps(self):
         return int(lib().orc_local_overlaps(self._h))
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions: hard spheres (eight checkerboard sets)
+# ---------------------------------------------------------------------------
+def _box3(L):
+    return np.ascontiguousarray(L, dtype=np.float64).reshape(3)
+
+
+def grid3(L, sigma=1.0):
+    """(m[3], w[3]) of the 3-d cell grid; ValueError if the box is invalid."""
+    Lb = _box3(L)
+    m = np.zeros(3, dtype=np.int32)
+    w = np.zeros(3, dtype=np.float64)
+    if lib().orc3_grid(_p(Lb, _f64p), sigma, _p(m, _i32p), _p(w, _f64p)):
+        raise ValueError("invalid box")
+    return m, w
+
+
+def lattice3_positions(N, L, sigma, seed):
+    Lb = _box3(L)
+    xyz = np.zeros(3 * N, dtype=np.float64)
+    if lib().orc3_lattice_positions(N, _p(Lb, _f64p), sigma, seed, _p(xyz, _f64p)):
+        raise ValueError("no fcc lattice for N = %d" % N)
+    return xyz.reshape(N, 3)
+
+
+def decode_perm8(n, k):
+    out = np.zeros(8, dtype=np.int32)
+    lib().orc3_decode_perm(n, k, _p(out, _i32p))
+    return out[:n]
+
+
+def sweep_draws3(seed, sweep, w):
+    wb = _box3(w)
+    perm = np.zeros(8, dtype=np.int32)
+    f = ctypes.c_int32()
+    ds = ctypes.c_double()
+    lib().orc3_sweep_draws(seed, sweep, _p(wb, _f64p), _p(perm, _i32p), ctypes.byref(f), ctypes.byref(ds))
+    return perm, f.value, ds.value
+
+
+def cell_draws3(seed, sweep, cell, Q, n, nsel, shuffle=True):
+    """(perm[:n], uvw[nsel, 3]) of one 3-d cell update."""
+    perm = np.zeros(8, dtype=np.int32)
+    uvw = np.zeros(3 * nsel, dtype=np.float64)
+    lib().orc3_cell_draws(seed, sweep, cell, Q, n, int(shuffle), nsel, _p(perm, _i32p), _p(uvw, _f64p))
+    return perm[:n], uvw.reshape(nsel, 3)
+
+
+def close_pairs3(xyz, L, rmin):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    Lb = _box3(L)
+    return int(lib().orc3_bruteforce_close_pairs(_p(xyz, _f64p), xyz.size // 3, _p(Lb, _f64p), rmin))
+
+
+def bruteforce_histogram3(xyz, L, sigma, nbins, dr):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    Lb = _box3(L)
+    h = np.zeros(nbins, dtype=np.uint64)
+    lib().orc3_bruteforce_histogram(_p(xyz, _f64p), xyz.size // 3, _p(Lb, _f64p), sigma, nbins, dr, _p(h, _u64p))
+    return h
+
+
+class System3:
+    """One hard-sphere system advanced by the oracle (three dimensions)."""
+
+    def __init__(self, N, L, sigma=1.0, d=0.1, nselect=4, seed=1, precision=FP64, xyz=None):
+        self._h = ctypes.c_void_p()
+        self.L = _box3(L).copy()
+        arg = None
+        if xyz is not None:
+            xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+            arg = _p(xyz, _f64p)
+        err = lib().orc3_create(ctypes.byref(self._h), N, _p(self.L, _f64p), sigma, d, nselect, seed,
+                                precision, arg)
+        if err:
+            raise OracleError(err, "create")
+        self.N, self.sigma, self.precision = N, sigma, precision
+        self.m, self.w, _, _ = self.info()
+        self.C = int(np.prod(self.m.astype(np.int64)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().orc3_destroy(h)
+            self._h = None
+
+    def info(self):
+        m = np.zeros(3, dtype=np.int32)
+        w = np.zeros(3, dtype=np.float64)
+        s, k = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().orc3_info(self._h, _p(m, _i32p), _p(w, _f64p), ctypes.byref(s), ctypes.byref(k))
+        return m, w, s.value, k.value
+
+    def sweep(self, n=1):
+        err = lib().orc3_sweep(self._h, n)
+        if err:
+            raise OracleError(err, "sweep")
+
+    def shift(self):
+        err = lib().orc3_shift(self._h)
+        if err:
+            raise OracleError(err, "shift")
+
+    def subsweep(self, sweep_index, Q):
+        lib().orc3_subsweep(self._h, sweep_index, Q)
+
+    def set_move_size(self, d):
+        if lib().orc3_set_move_size(self._h, d):
+            raise ValueError("bad move size")
+
+    def set_balance(self, shuffle_particles=True, shuffle_sets=True):
+        lib().orc3_set_balance(self._h, int(shuffle_particles), int(shuffle_sets))
+
+    def counters(self):
+        out = np.zeros(4, dtype=np.uint64)
+        lib().orc3_counters(self._h, _p(out, _u64p))
+        return out
+
+    def origin(self):
+        out = np.zeros(3, dtype=np.float64)
+        lib().orc3_origin(self._h, _p(out, _f64p))
+        return out
+
+    def state(self):
+        """(local[C,8,3] float64, counts[C] uint8), c = (cz*my + cy)*mx + cx."""
+        loc = np.zeros(self.C * 24, dtype=np.float64)
+        cnt = np.zeros(self.C, dtype=np.uint8)
+        lib().orc3_state(self._h, _p(loc, _f64p), _p(cnt, _u8p))
+        return loc.reshape(self.C, 8, 3), cnt
+
+    def positions(self):
+        xyz = np.zeros(3 * self.N, dtype=np.float64)
+        lib().orc3_positions(self._h, _p(xyz, _f64p))
+        return xyz.reshape(self.N, 3)
+
+    def box(self):
+        """Periodic box of the mode's geometry (binary32 cell widths in FP32 mode)."""
+        if self.precision == FP64:
+            return self.L.copy()
+        return self.m * self.w.astype(np.float32).astype(np.float64)
+
+    def histogram(self, nbins=200, dr=pressure.DR):
+        h = np.zeros(nbins, dtype=np.uint64)
+        lib().orc3_histogram(self._h, nbins, dr * self.sigma, _p(h, _u64p))
+        return h
+
+    def local_overlaps(self):
+        return int(lib().orc3_local_overlaps(self._h))

@@ -1223,3 +1223,707 @@ int orc_set_threads(int n)
 }
 
 int orc_local_overlaps(const oracle_t *o) { return (int)count_overlaps_local(o); }
+
+/* ======================================================================== */
+/* Three dimensions: N hard spheres of diameter sigma in a periodic          */
+/* Lx x Ly x Lz box.  The method is the same with cubic cells and eight      */
+/* checkerboard sets Q = (cx mod 2) + 2 (cy mod 2) + 4 (cz mod 2) (Sec. 2.1, */
+/* Sec. 2.2: eight sub-sweeps per sweep in three dimensions; Sec. 6).       */
+/* Readings (the paper gives the 3-d case in words only):                   */
+/*  - grid: m_a = largest even integer <= L_a/sigma per axis (>= 4), and     */
+/*    wx^2 + wy^2 + wz^2 < 4 sigma^2, so that each of the cell's eight half- */
+/*    size boxes holds at most one centre: n <= 8 per cell;                 */
+/*  - trial displacement uniform in a ball of radius d (the "maximum move    */
+/*    radius" of Sec. 3.3), by rejection from (-1,1)^3;                     */
+/*  - the shift direction is one of +-x, +-y, +-z (Alg. 4 with three axes); */
+/*  - binary32 mode: the same binary64 draws, rounded to binary32 for the   */
+/*    move; positions, widths and pair tests in binary32 as in two          */
+/*    dimensions (trial position and overlap predicate by fma).             */
+/* ======================================================================== */
+#define NMAX3 8
+
+typedef struct oracle3 {
+    int64_t N;
+    double L[3], sigma, d;
+    int nsel;
+    uint64_t seed;
+    int prec;
+    int m[3];
+    double w[3];            /* cell widths, binary64 */
+    float wf[3];            /* binary32 cell widths (FP32 mode) */
+    int64_t C;              /* mx*my*mz */
+    double *P;              /* FP64: coordinate a of slot (c,j) at P[3(8c+j)+a], c = (cz my + cy) mx + cx */
+    float *Pf;              /* FP32 */
+    uint8_t *n;
+    double O[3];            /* accumulated grid origin */
+    uint64_t sweep, shifts;
+    uint64_t cnt[4];        /* trials, accepted, rejected (left cell), rejected (overlap) */
+    int shuffle_particles, shuffle_sets;
+} oracle3_t;
+
+static const uint32_t kFactorial8[9] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 40320u};
+
+/* Fisher-Yates decode of k in [0, n!) for n <= 8 (same rule as decode_perm). */
+static void decode_perm8(int n, uint32_t k, int perm[8])
+{
+    for (int j = 0; j < 8; ++j) perm[j] = j;
+    for (int j = n - 1; j >= 1; --j) {
+        int r = (int)(k % (uint32_t)(j + 1));
+        k /= (uint32_t)(j + 1);
+        int t = perm[j]; perm[j] = perm[r]; perm[r] = t;
+    }
+}
+
+void orc3_decode_perm(int n, uint32_t k, int32_t out[8])
+{
+    int p[8];
+    decode_perm8(n, k, p);
+    for (int j = 0; j < 8; ++j) out[j] = p[j];
+}
+
+int orc3_grid(const double L[3], double sigma, int32_t m[3], double w[3])
+{
+    if (!(sigma > 0)) return ORC_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (!(L[a] > 0)) return ORC_EINVAL;
+        int q = grid_size(L[a], sigma);
+        if (q < 4) return ORC_EINVAL;
+        m[a] = q;
+        w[a] = L[a] / q;
+    }
+    if ((int64_t)m[0] * m[1] * m[2] >= ((int64_t)1 << 32)) return ORC_EINVAL;
+    if (!((w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] < 4.0 * sigma * sigma)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+void orc3_destroy(oracle3_t *o)
+{
+    if (!o) return;
+    free(o->P); free(o->Pf); free(o->n);
+    free(o);
+}
+
+static oracle3_t *alloc_state3(int64_t N, const double L[3], double sigma, double d, int nsel,
+                               uint64_t seed, int prec, int *err)
+{
+    int32_t m[3];
+    double w[3];
+    *err = ORC_EINVAL;
+    if (N < 1 || nsel < 1 || nsel > 255 || (prec != 0 && prec != 1)) return NULL;
+    if (orc3_grid(L, sigma, m, w) != ORC_OK) return NULL;
+    for (int a = 0; a < 3; ++a)
+        if (!(d > 0) || !(d < 0.5 * w[a])) return NULL;
+    int64_t C = (int64_t)m[0] * m[1] * m[2];
+    if (C * NMAX3 < N) return NULL;
+    oracle3_t *o = (oracle3_t *)calloc(1, sizeof(oracle3_t));
+    *err = ORC_ENOMEM;
+    if (!o) return NULL;
+    o->N = N; o->sigma = sigma; o->d = d; o->nsel = nsel; o->seed = seed; o->prec = prec;
+    for (int a = 0; a < 3; ++a) { o->L[a] = L[a]; o->m[a] = m[a]; o->w[a] = w[a]; o->wf[a] = (float)w[a]; }
+    o->C = C;
+    o->shuffle_particles = 1; o->shuffle_sets = 1;
+    o->n = (uint8_t *)calloc((size_t)C, 1);
+    if (prec == 0) o->P = (double *)malloc(sizeof(double) * 3 * NMAX3 * (size_t)C);
+    else o->Pf = (float *)malloc(sizeof(float) * 3 * NMAX3 * (size_t)C);
+    if (!o->n || (prec == 0 ? !o->P : !o->Pf)) { orc3_destroy(o); return NULL; }
+    *err = ORC_OK;
+    return o;
+}
+
+static int64_t cell3(const oracle3_t *o, int cx, int cy, int cz)
+{
+    return ((int64_t)cz * o->m[1] + cy) * o->m[0] + cx;
+}
+
+static double slot3(const oracle3_t *o, int64_t c, int j, int a)
+{
+    return o->prec == 0 ? o->P[3 * (NMAX3 * c + j) + a] : (double)o->Pf[3 * (NMAX3 * c + j) + a];
+}
+
+/* binary32 overlap predicate in three dimensions:
+ * fma(dx, dx, fma(dy, dy, fma(dz, dz, -sigma^2))) < 0. */
+static int overlap3_32(float dx, float dy, float dz, float sig2)
+{
+    return fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, -sig2))) < 0.0f;
+}
+
+/* binary64 overlap predicate: (dx*dx + dy*dy) + dz*dz < sigma^2. */
+static int overlap3_64(double dx, double dy, double dz, double sig2)
+{
+    return (dx * dx + dy * dy) + dz * dz < sig2;
+}
+
+/* Ordered overlapping pairs over each sphere's 27-cell neighbourhood, in
+ * cell-local frames with the sweep's arithmetic. */
+static int64_t count_overlaps_local3(const oracle3_t *o)
+{
+    int64_t bad = 0;
+    for (int cz = 0; cz < o->m[2]; ++cz)
+        for (int cy = 0; cy < o->m[1]; ++cy)
+            for (int cx = 0; cx < o->m[0]; ++cx) {
+                int64_t c = cell3(o, cx, cy, cz);
+                for (int i = 0; i < o->n[c]; ++i)
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int64_t nc = cell3(o, (cx + dx + o->m[0]) % o->m[0], (cy + dy + o->m[1]) % o->m[1],
+                                                   (cz + dz + o->m[2]) % o->m[2]);
+                                for (int j = 0; j < o->n[nc]; ++j) {
+                                    if (dx == 0 && dy == 0 && dz == 0 && j == i) continue;
+                                    if (o->prec == 0) {
+                                        double e0 = slot3(o, nc, j, 0) + (double)dx * o->w[0];
+                                        double e1 = slot3(o, nc, j, 1) + (double)dy * o->w[1];
+                                        double e2 = slot3(o, nc, j, 2) + (double)dz * o->w[2];
+                                        if (overlap3_64(slot3(o, c, i, 0) - e0, slot3(o, c, i, 1) - e1,
+                                                        slot3(o, c, i, 2) - e2, o->sigma * o->sigma))
+                                            bad++;
+                                    } else {
+                                        float e0 = (float)slot3(o, nc, j, 0) + (float)dx * o->wf[0];
+                                        float e1 = (float)slot3(o, nc, j, 1) + (float)dy * o->wf[1];
+                                        float e2 = (float)slot3(o, nc, j, 2) + (float)dz * o->wf[2];
+                                        if (overlap3_32((float)slot3(o, c, i, 0) - e0, (float)slot3(o, c, i, 1) - e1,
+                                                        (float)slot3(o, c, i, 2) - e2,
+                                                        (float)(o->sigma * o->sigma)))
+                                            bad++;
+                                    }
+                                }
+                            }
+            }
+    return bad;
+}
+
+/* Place global positions xyz[3N] into the cells (slot order = particle
+ * order), with the same binning rule as in two dimensions. */
+static int place3(oracle3_t *o, const double *xyz)
+{
+    memset(o->n, 0, (size_t)o->C);
+    for (int64_t k = 0; k < 3 * NMAX3 * o->C; ++k) {
+        if (o->prec == 0) o->P[k] = EMPTY_SLOT;
+        else o->Pf[k] = (float)EMPTY_SLOT;
+    }
+    for (int64_t p = 0; p < o->N; ++p) {
+        int cc[3];
+        double l[3];
+        for (int a = 0; a < 3; ++a) {
+            double x = xyz[3 * p + a];
+            if (!(x >= 0.0 && x <= o->L[a])) return ORC_EINVAL;
+            bin_axis(x, o->w[a], o->m[a], &cc[a], &l[a]);
+        }
+        int64_t c = cell3(o, cc[0], cc[1], cc[2]);
+        if (o->n[c] >= NMAX3) return ORC_EOVERFLOW;
+        int j = o->n[c]++;
+        for (int a = 0; a < 3; ++a) {
+            if (o->prec == 0) o->P[3 * (NMAX3 * c + j) + a] = l[a];
+            else {
+                float f = (float)l[a];
+                if (f >= o->wf[a]) f = prev_float(o->wf[a]);
+                o->Pf[3 * (NMAX3 * c + j) + a] = f;
+            }
+        }
+    }
+    if (count_overlaps_local3(o) != 0) return ORC_EOVERLAP;
+    return ORC_OK;
+}
+
+/* Face-centred cubic start: N = 4 q^3; unit cell b = (i,j,k) of side L_a/q
+ * along axis a holds the sites (b + s + 1/4) L_a/q for the four basis
+ * vectors s = (0,0,0), (1/2,1/2,0), (1/2,0,1/2), (0,1/2,1/2); site
+ * p = 4((k q + j) q + i) + s is displaced uniformly within a ball of radius
+ * 0.01 sigma (init stream of p, attempts of six words, binary64) and
+ * wrapped into the box. */
+int orc3_lattice_positions(int64_t N, const double L[3], double sigma, uint64_t seed, double *xyz)
+{
+    int64_t q = 1;
+    while (4 * q * q * q < N) ++q;
+    if (N < 4 || 4 * q * q * q != N) return ORC_EINVAL;
+    static const double basis[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    const double rj = 0.01 * sigma;
+    for (int64_t k = 0; k < q; ++k)
+        for (int64_t j = 0; j < q; ++j)
+            for (int64_t i = 0; i < q; ++i)
+                for (int s = 0; s < 4; ++s) {
+                    int64_t p = 4 * ((k * q + j) * q + i) + s;
+                    const int64_t b[3] = {i, j, k};
+                    stream_t st;
+                    stream_open(&st, seed, (uint32_t)p, 0xFFFFFFFEu, DOM_INIT << 28);
+                    double u[3];
+                    do {
+                        for (int a = 0; a < 3; ++a) {
+                            uint32_t hi = stream_word(&st), lo = stream_word(&st);
+                            u[a] = sym52(hi, lo);
+                        }
+                    } while (!((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] < 1.0));
+                    for (int a = 0; a < 3; ++a) {
+                        double x = ((double)b[a] + basis[s][a] + 0.25) * (L[a] / (double)q) + rj * u[a];
+                        if (x >= L[a]) x -= L[a];
+                        if (x < 0.0) x += L[a];
+                        xyz[3 * p + a] = x;
+                    }
+                }
+    return ORC_OK;
+}
+
+int orc3_create(oracle3_t **out, int64_t N, const double L[3], double sigma, double d, int nsel,
+                uint64_t seed, int prec, const double *xyz)
+{
+    int err;
+    *out = NULL;
+    oracle3_t *o = alloc_state3(N, L, sigma, d, nsel, seed, prec, &err);
+    if (!o) return err;
+    if (xyz) {
+        err = place3(o, xyz);
+    } else {
+        double *buf = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+        if (!buf) { orc3_destroy(o); return ORC_ENOMEM; }
+        err = orc3_lattice_positions(N, L, sigma, seed, buf);
+        if (err == ORC_OK) err = place3(o, buf);
+        free(buf);
+    }
+    if (err != ORC_OK) { orc3_destroy(o); return err; }
+    *out = o;
+    return ORC_OK;
+}
+
+int orc3_set_move_size(oracle3_t *o, double d)
+{
+    for (int a = 0; a < 3; ++a)
+        if (!(d > 0) || !(d < 0.5 * o->w[a])) return ORC_EINVAL;
+    o->d = d;
+    return ORC_OK;
+}
+
+void orc3_set_balance(oracle3_t *o, int shuffle_particles, int shuffle_sets)
+{
+    o->shuffle_particles = shuffle_particles;
+    o->shuffle_sets = shuffle_sets;
+}
+
+/* Sweep-level draws: order of the eight sets by Fisher-Yates (j = 7..1,
+ * k = bounded(j+1)), direction f = bounded(6) (f>>1 the axis, f&1 set for
+ * the negative direction), distance unif53 * w_axis/2.  Explicit shifts draw
+ * f and the distance from their own stream. */
+typedef struct { int perm[8]; int fdir; double ds; } draws3_t;
+
+static void sweep_draws3(uint64_t seed, uint32_t sweep, const double w[3], draws3_t *r)
+{
+    stream_t s;
+    stream_open(&s, seed, sweep, 0xFFFFFFFFu, DOM_SWEEP << 28);
+    for (int q = 0; q < 8; ++q) r->perm[q] = q;
+    for (int j = 7; j >= 1; --j) {
+        int k = (int)stream_bounded(&s, (uint32_t)(j + 1));
+        int t = r->perm[j]; r->perm[j] = r->perm[k]; r->perm[k] = t;
+    }
+    r->fdir = (int)stream_bounded(&s, 6u);
+    uint32_t hi = stream_word(&s), lo = stream_word(&s);
+    r->ds = unif53(hi, lo) * (0.5 * w[r->fdir >> 1]);
+}
+
+static void shift_draws3(uint64_t seed, uint32_t index, const double w[3], draws3_t *r)
+{
+    stream_t s;
+    stream_open(&s, seed, index, 0xFFFFFFFFu, DOM_SHIFT << 28);
+    for (int q = 0; q < 8; ++q) r->perm[q] = q;
+    r->fdir = (int)stream_bounded(&s, 6u);
+    uint32_t hi = stream_word(&s), lo = stream_word(&s);
+    r->ds = unif53(hi, lo) * (0.5 * w[r->fdir >> 1]);
+}
+
+void orc3_sweep_draws(uint64_t seed, uint32_t sweep, const double w[3], int32_t perm[8], int32_t *fdir, double *ds)
+{
+    draws3_t r;
+    sweep_draws3(seed, sweep, w, &r);
+    for (int q = 0; q < 8; ++q) perm[q] = r.perm[q];
+    *fdir = r.fdir;
+    *ds = r.ds;
+}
+
+/* Draws of one cell update (sweep s, set Q, canonical cell c): shuffle
+ * stream S = (s, c, (0<<28)|(Q<<24)) gives k = bounded(n!) when n >= 2 and
+ * the particle shuffle is on; trial stream T = (s, c, (1<<28)|(Q<<24)) is
+ * read as consecutive words, six per attempt: u = sym52(w0,w1),
+ * v = sym52(w2,w3), s = sym52(w4,w5), kept when (u*u + v*v) + s*s < 1. */
+static void cell_draws3(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
+                        int perm[8], double *U)
+{
+    const uint32_t setbits = (uint32_t)Q << 24;
+    for (int j = 0; j < 8; ++j) perm[j] = j;
+    if (shuffle && n >= 2) {
+        stream_t s;
+        stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | setbits);
+        decode_perm8(n, stream_bounded(&s, kFactorial8[n]), perm);
+    }
+    stream_t t;
+    stream_open(&t, seed, sweep, cell, (DOM_TRIAL << 28) | setbits);
+    for (int k = 0; k < nsel;) {
+        double u[3];
+        for (int a = 0; a < 3; ++a) {
+            uint32_t hi = stream_word(&t), lo = stream_word(&t);
+            u[a] = sym52(hi, lo);
+        }
+        if ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] < 1.0) {
+            U[3 * k] = u[0]; U[3 * k + 1] = u[1]; U[3 * k + 2] = u[2];
+            ++k;
+        }
+    }
+}
+
+/* Test hook: the draws of one cell update (perm[8], uvw[3*nsel]). */
+void orc3_cell_draws(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
+                     int32_t perm[8], double *uvw)
+{
+    int p[8];
+    cell_draws3(seed, sweep, cell, Q, n, shuffle, nsel, p, uvw);
+    for (int j = 0; j < 8; ++j) perm[j] = p[j];
+}
+
+/* One cell update (Alg. 1, Alg. 2 in three dimensions). */
+static void cell_update3(oracle3_t *o, uint32_t sweep, int Q, int cx, int cy, int cz, uint64_t acc[4])
+{
+    int64_t c = cell3(o, cx, cy, cz);
+    int n = o->n[c];
+    if (n == 0) return;
+    int perm[8];
+    double U[3 * 256];
+    cell_draws3(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, perm, U);
+    const int cc[3] = {cx, cy, cz};
+    if (o->prec == 0) {
+        double *X = o->P + 3 * NMAX3 * c;
+        double tmp[3 * NMAX3];
+        for (int j = 0; j < n; ++j)
+            for (int a = 0; a < 3; ++a) tmp[3 * j + a] = X[3 * perm[j] + a];
+        for (int j = 0; j < 3 * n; ++j) X[j] = tmp[j];
+        const double sig2 = o->sigma * o->sigma;
+        for (int t = 0; t < o->nsel; ++t) {
+            int i = visit_slot(t, n);
+            double p[3];
+            int inside = 1;
+            for (int a = 0; a < 3; ++a) {
+                p[a] = X[3 * i + a] + o->d * U[3 * t + a];
+                if (!(p[a] >= 0.0 && p[a] < o->w[a])) inside = 0;
+            }
+            acc[0]++;
+            if (!inside) { acc[2]++; continue; }
+            int overlap = 0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                if (overlap3_64(p[0] - X[3 * j], p[1] - X[3 * j + 1], p[2] - X[3 * j + 2], sig2)) overlap = 1;
+            }
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx == 0 && dy == 0 && dz == 0) continue;
+                        const int dd[3] = {dx, dy, dz};
+                        int nn[3];
+                        for (int a = 0; a < 3; ++a) nn[a] = (cc[a] + dd[a] + o->m[a]) % o->m[a];
+                        int64_t nc = cell3(o, nn[0], nn[1], nn[2]);
+                        const double *Y = o->P + 3 * NMAX3 * nc;
+                        for (int j = 0; j < o->n[nc]; ++j) {
+                            double e[3];
+                            for (int a = 0; a < 3; ++a) e[a] = Y[3 * j + a] + (double)dd[a] * o->w[a];
+                            if (overlap3_64(p[0] - e[0], p[1] - e[1], p[2] - e[2], sig2)) overlap = 1;
+                        }
+                    }
+            if (overlap) { acc[3]++; continue; }
+            for (int a = 0; a < 3; ++a) X[3 * i + a] = p[a];
+            acc[1]++;
+        }
+    } else {
+        float *X = o->Pf + 3 * NMAX3 * c;
+        float tmp[3 * NMAX3];
+        for (int j = 0; j < n; ++j)
+            for (int a = 0; a < 3; ++a) tmp[3 * j + a] = X[3 * perm[j] + a];
+        for (int j = 0; j < 3 * n; ++j) X[j] = tmp[j];
+        const float sig2 = (float)(o->sigma * o->sigma);
+        const float df = (float)o->d;
+        for (int t = 0; t < o->nsel; ++t) {
+            int i = visit_slot(t, n);
+            float p[3];
+            int inside = 1;
+            for (int a = 0; a < 3; ++a) {
+                p[a] = fmaf(df, (float)U[3 * t + a], X[3 * i + a]);
+                if (!(p[a] >= 0.0f && p[a] < o->wf[a])) inside = 0;
+            }
+            acc[0]++;
+            if (!inside) { acc[2]++; continue; }
+            int overlap = 0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                if (overlap3_32(p[0] - X[3 * j], p[1] - X[3 * j + 1], p[2] - X[3 * j + 2], sig2)) overlap = 1;
+            }
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx == 0 && dy == 0 && dz == 0) continue;
+                        const int dd[3] = {dx, dy, dz};
+                        int nn[3];
+                        for (int a = 0; a < 3; ++a) nn[a] = (cc[a] + dd[a] + o->m[a]) % o->m[a];
+                        int64_t nc = cell3(o, nn[0], nn[1], nn[2]);
+                        const float *Y = o->Pf + 3 * NMAX3 * nc;
+                        for (int j = 0; j < o->n[nc]; ++j) {
+                            float e[3];
+                            for (int a = 0; a < 3; ++a) e[a] = Y[3 * j + a] + (float)dd[a] * o->wf[a];
+                            if (overlap3_32(p[0] - e[0], p[1] - e[1], p[2] - e[2], sig2)) overlap = 1;
+                        }
+                    }
+            if (overlap) { acc[3]++; continue; }
+            for (int a = 0; a < 3; ++a) X[3 * i + a] = p[a];
+            acc[1]++;
+        }
+    }
+}
+
+/* All cells of set Q (independent of each other). */
+static void subsweep3(oracle3_t *o, uint32_t sweep, int Q)
+{
+    int qx = Q & 1, qy = (Q >> 1) & 1, qz = Q >> 2;
+    uint64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3)
+#endif
+    for (int cz = qz; cz < o->m[2]; cz += 2) {
+        uint64_t acc[4] = {0, 0, 0, 0};
+        for (int cy = qy; cy < o->m[1]; cy += 2)
+            for (int cx = qx; cx < o->m[0]; cx += 2) cell_update3(o, sweep, Q, cx, cy, cz, acc);
+        t0 += acc[0]; t1 += acc[1]; t2 += acc[2]; t3 += acc[3];
+    }
+    o->cnt[0] += t0; o->cnt[1] += t1; o->cnt[2] += t2; o->cnt[3] += t3;
+}
+
+/* Cell shift (Alg. 4) along one of three axes, the same rule as in two
+ * dimensions: new cell c keeps the spheres of old c that stay inside it, in
+ * slot order, then takes those of old c+f that leave c+f, re-expressed in
+ * c's frame and clamped into [0, w). */
+static int shift_cells3(oracle3_t *o, int fdir, double ds)
+{
+    const int ax = fdir >> 1;
+    const int sgn = (fdir & 1) ? -1 : 1;
+    const int64_t C = o->C;
+    uint8_t *nn = (uint8_t *)calloc((size_t)C, 1);
+    double *NP = NULL;
+    float *NPf = NULL;
+    if (o->prec == 0) NP = (double *)malloc(sizeof(double) * 3 * NMAX3 * (size_t)C);
+    else NPf = (float *)malloc(sizeof(float) * 3 * NMAX3 * (size_t)C);
+    if (!nn || (o->prec == 0 ? !NP : !NPf)) { free(nn); free(NP); free(NPf); return ORC_ENOMEM; }
+    int overflow = 0;
+    for (int cz = 0; cz < o->m[2]; ++cz)
+        for (int cy = 0; cy < o->m[1]; ++cy)
+            for (int cx = 0; cx < o->m[0]; ++cx) {
+                int64_t c = cell3(o, cx, cy, cz);
+                int nb3[3] = {cx, cy, cz};
+                nb3[ax] = (nb3[ax] + sgn + o->m[ax]) % o->m[ax];
+                int64_t nb = cell3(o, nb3[0], nb3[1], nb3[2]);
+                int k = 0;
+                if (o->prec == 0) {
+                    const double w = o->w[ax], sd = (double)sgn * ds, sw = (double)sgn * w;
+                    double tmp[3 * (2 * NMAX3)];
+                    for (int j = 0; j < o->n[c]; ++j) {
+                        const double *p = o->P + 3 * (NMAX3 * c + j);
+                        double dp = p[ax] - sd;
+                        if (dp >= 0.0 && dp < w) {
+                            for (int a = 0; a < 3; ++a) tmp[3 * k + a] = p[a];
+                            tmp[3 * k + ax] = dp;
+                            k++;
+                        }
+                    }
+                    for (int j = 0; j < o->n[nb]; ++j) {
+                        const double *p = o->P + 3 * (NMAX3 * nb + j);
+                        double dp = p[ax] - sd;
+                        if (!(dp >= 0.0 && dp < w)) {
+                            double v = dp + sw;
+                            if (v >= w) v = prev_double(w);
+                            if (v < 0.0) v = 0.0;
+                            for (int a = 0; a < 3; ++a) tmp[3 * k + a] = p[a];
+                            tmp[3 * k + ax] = v;
+                            k++;
+                        }
+                    }
+                    if (k > NMAX3) { overflow = 1; k = NMAX3; }
+                    for (int j = 0; j < 3 * NMAX3; ++j) NP[3 * NMAX3 * c + j] = j < 3 * k ? tmp[j] : EMPTY_SLOT;
+                } else {
+                    const float w = o->wf[ax], sd = (float)sgn * (float)ds, sw = (float)sgn * w;
+                    float tmp[3 * (2 * NMAX3)];
+                    for (int j = 0; j < o->n[c]; ++j) {
+                        const float *p = o->Pf + 3 * (NMAX3 * c + j);
+                        float dp = p[ax] - sd;
+                        if (dp >= 0.0f && dp < w) {
+                            for (int a = 0; a < 3; ++a) tmp[3 * k + a] = p[a];
+                            tmp[3 * k + ax] = dp;
+                            k++;
+                        }
+                    }
+                    for (int j = 0; j < o->n[nb]; ++j) {
+                        const float *p = o->Pf + 3 * (NMAX3 * nb + j);
+                        float dp = p[ax] - sd;
+                        if (!(dp >= 0.0f && dp < w)) {
+                            float v = dp + sw;
+                            if (v >= w) v = prev_float(w);
+                            if (v < 0.0f) v = 0.0f;
+                            for (int a = 0; a < 3; ++a) tmp[3 * k + a] = p[a];
+                            tmp[3 * k + ax] = v;
+                            k++;
+                        }
+                    }
+                    if (k > NMAX3) { overflow = 1; k = NMAX3; }
+                    for (int j = 0; j < 3 * NMAX3; ++j)
+                        NPf[3 * NMAX3 * c + j] = j < 3 * k ? tmp[j] : (float)EMPTY_SLOT;
+                }
+                nn[c] = (uint8_t)k;
+            }
+    if (o->prec == 0) {
+        free(o->P);
+        o->P = NP;
+        o->O[ax] += (double)sgn * ds;
+    } else {
+        free(o->Pf);
+        o->Pf = NPf;
+        o->O[ax] += (double)((float)sgn * (float)ds);
+    }
+    free(o->n);
+    o->n = nn;
+    return overflow ? ORC_EOVERFLOW : ORC_OK;
+}
+
+int orc3_sweep(oracle3_t *o, int64_t nsweeps)
+{
+    for (int64_t k = 0; k < nsweeps; ++k) {
+        uint32_t sweep = (uint32_t)o->sweep;
+        draws3_t r;
+        sweep_draws3(o->seed, sweep, o->w, &r);
+        for (int q = 0; q < 8; ++q) subsweep3(o, sweep, o->shuffle_sets ? r.perm[q] : q);
+        int err = shift_cells3(o, r.fdir, r.ds);
+        o->sweep += 1;
+        if (err != ORC_OK) return err;
+    }
+    return ORC_OK;
+}
+
+int orc3_shift(oracle3_t *o)
+{
+    draws3_t r;
+    shift_draws3(o->seed, (uint32_t)o->shifts, o->w, &r);
+    o->shifts += 1;
+    return shift_cells3(o, r.fdir, r.ds);
+}
+
+void orc3_subsweep(oracle3_t *o, uint32_t sweep, int Q) { subsweep3(o, sweep, Q); }
+
+void orc3_info(const oracle3_t *o, int32_t m[3], double w[3], uint64_t *sweep, uint64_t *shifts)
+{
+    for (int a = 0; a < 3; ++a) { m[a] = o->m[a]; w[a] = o->w[a]; }
+    *sweep = o->sweep;
+    *shifts = o->shifts;
+}
+
+void orc3_counters(const oracle3_t *o, uint64_t out[4])
+{
+    for (int k = 0; k < 4; ++k) out[k] = o->cnt[k];
+}
+
+void orc3_origin(const oracle3_t *o, double out[3])
+{
+    for (int a = 0; a < 3; ++a) out[a] = o->O[a];
+}
+
+/* Raw state: local[3(8c+j)+a] (EMPTY_SLOT where unused), counts[c]. */
+void orc3_state(const oracle3_t *o, double *local, uint8_t *counts)
+{
+    for (int64_t c = 0; c < o->C; ++c) {
+        counts[c] = o->n[c];
+        for (int j = 0; j < NMAX3; ++j)
+            for (int a = 0; a < 3; ++a)
+                local[3 * (NMAX3 * c + j) + a] = j < o->n[c] ? slot3(o, c, j, a) : EMPTY_SLOT;
+    }
+}
+
+/* Global coordinates in canonical (cell, slot) order:
+ * g = O + (cell*w + local) wrapped into [0, m*w) (binary32 widths in FP32 mode). */
+void orc3_positions(const oracle3_t *o, double *xyz)
+{
+    double w[3], L[3];
+    for (int a = 0; a < 3; ++a) {
+        w[a] = o->prec == 0 ? o->w[a] : (double)o->wf[a];
+        L[a] = o->prec == 0 ? o->L[a] : (double)o->m[a] * w[a];
+    }
+    int64_t p = 0;
+    for (int cz = 0; cz < o->m[2]; ++cz)
+        for (int cy = 0; cy < o->m[1]; ++cy)
+            for (int cx = 0; cx < o->m[0]; ++cx) {
+                int64_t c = cell3(o, cx, cy, cz);
+                const int cc[3] = {cx, cy, cz};
+                for (int j = 0; j < o->n[c]; ++j) {
+                    for (int a = 0; a < 3; ++a) {
+                        double g = o->O[a] + ((double)cc[a] * w[a] + slot3(o, c, j, a));
+                        xyz[3 * p + a] = g - L[a] * floor(g / L[a]);
+                    }
+                    p++;
+                }
+            }
+}
+
+/* Contact histogram in three dimensions: ordered pairs at distance r with
+ * sigma <= r < sigma + nbins*dr over the 5x5x5 cell neighbourhood, binary64,
+ * squared distance (dx*dx + dy*dy) + dz*dz, bins as in two dimensions. */
+void orc3_histogram(const oracle3_t *o, int nbins, double dr, uint64_t *hist)
+{
+    memset(hist, 0, sizeof(uint64_t) * (size_t)nbins);
+    double w[3];
+    for (int a = 0; a < 3; ++a) w[a] = o->prec == 0 ? o->w[a] : (double)o->wf[a];
+    for (int cz = 0; cz < o->m[2]; ++cz)
+        for (int cy = 0; cy < o->m[1]; ++cy)
+            for (int cx = 0; cx < o->m[0]; ++cx) {
+                int64_t c = cell3(o, cx, cy, cz);
+                const int cc[3] = {cx, cy, cz};
+                for (int i = 0; i < o->n[c]; ++i)
+                    for (int dz = -2; dz <= 2; ++dz)
+                        for (int dy = -2; dy <= 2; ++dy)
+                            for (int dx = -2; dx <= 2; ++dx) {
+                                const int dd[3] = {dx, dy, dz};
+                                int nn[3];
+                                for (int a = 0; a < 3; ++a) nn[a] = ((cc[a] + dd[a]) % o->m[a] + o->m[a]) % o->m[a];
+                                int64_t nc = cell3(o, nn[0], nn[1], nn[2]);
+                                for (int j = 0; j < o->n[nc]; ++j) {
+                                    if (dx == 0 && dy == 0 && dz == 0 && j == i) continue;
+                                    double e[3];
+                                    for (int a = 0; a < 3; ++a)
+                                        e[a] = slot3(o, c, i, a) - (slot3(o, nc, j, a) + (double)dd[a] * w[a]);
+                                    int b = bin_of_r2((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2], o->sigma, dr, nbins);
+                                    if (b >= 0) hist[b] += 1;
+                                }
+                            }
+            }
+}
+
+int orc3_local_overlaps(const oracle3_t *o) { return (int)count_overlaps_local3(o); }
+
+/* Brute force on global coordinates over all pairs and the 27 periodic
+ * images (tests): unordered pairs closer than rmin, and the ordered-pair
+ * distance histogram with the rule above. */
+int64_t orc3_bruteforce_close_pairs(const double *xyz, int64_t N, const double L[3], double rmin)
+{
+    int64_t bad = 0;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i + 1; j < N; ++j) {
+            double e[3];
+            for (int a = 0; a < 3; ++a) e[a] = min_image(xyz[3 * i + a] - xyz[3 * j + a], L[a]);
+            if ((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2] < rmin * rmin) bad++;
+        }
+    return bad;
+}
+
+void orc3_bruteforce_histogram(const double *xyz, int64_t N, const double L[3], double sigma, int nbins,
+                               double dr, uint64_t *hist)
+{
+    memset(hist, 0, sizeof(uint64_t) * (size_t)nbins);
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j)
+            for (int iz = -1; iz <= 1; ++iz)
+                for (int iy = -1; iy <= 1; ++iy)
+                    for (int ix = -1; ix <= 1; ++ix) {
+                        if (i == j && ix == 0 && iy == 0 && iz == 0) continue;
+                        const int ii[3] = {ix, iy, iz};
+                        double e[3];
+                        for (int a = 0; a < 3; ++a) e[a] = xyz[3 * i + a] - (xyz[3 * j + a] + (double)ii[a] * L[a]);
+                        int b = bin_of_r2((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2], sigma, dr, nbins);
+                        if (b >= 0) hist[b] += 1;
+                    }
+}

@@ -102,3 +102,56 @@ def uniform_points(N: int, Lx: float, Ly: float, seed: int) -> np.ndarray:
     xy[:, 0] = rng.uniform(0.0, Lx, N)
     xy[:, 1] = rng.uniform(0.0, Ly, N)
     return xy
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions (hard spheres).  Packing fraction phi = N pi sigma^3 /
+# (6 V); the start is a face-centred cubic lattice of q^3 unit cells,
+# N = 4 q^3, filling a cubic box.
+# ---------------------------------------------------------------------------
+@dataclass
+class Workload3:
+    name: str
+    N: int
+    L: tuple
+    d: float
+    nselect: int
+    seed: int
+    sweeps: int
+    precision: str = "fp64"
+    sigma: float = 1.0
+    phi: float = 0.0
+
+
+def cube_box3(N: int, phi: float, sigma: float = 1.0):
+    a = (N * math.pi * sigma**3 / (6.0 * phi)) ** (1.0 / 3.0)
+    return (a, a, a)
+
+
+def fcc3(q: int, phi: float, d: float, seed: int = 1, precision: str = "fp64", nselect: int = 4,
+         sweeps: int = 100) -> Workload3:
+    N = 4 * q**3
+    return Workload3("spheres_n%d_phi%.3f_fcc" % (N, phi), N, cube_box3(N, phi), d, nselect, seed, sweeps,
+                     precision, phi=phi)
+
+
+def spheres_n2048_phi045() -> Workload3:
+    """N = 4*8^3 spheres, phi = 0.45 (dense fluid), d = 0.1: 12^3 cells."""
+    return fcc3(8, 0.45, 0.10)
+
+
+def spheres_n16384_phi045() -> Workload3:
+    """N = 4*16^3 spheres, phi = 0.45, d = 0.1: 26^3 cells."""
+    return fcc3(16, 0.45, 0.10)
+
+
+def spheres_n1m_phi049(precision: str = "fp32") -> Workload3:
+    """N = 4*64^3 = 1,048,576 spheres at the freezing packing fraction
+    phi = 0.49, d = 0.08, n_M = 4: 102^3 cells."""
+    return fcc3(64, 0.49, 0.08, precision=precision, sweeps=10000)
+
+
+def uniform_points3(N: int, L, seed: int) -> np.ndarray:
+    """N independent uniform points in the box [0,Lx) x [0,Ly) x [0,Lz)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.0, L[a], N) for a in range(3)], axis=1)
