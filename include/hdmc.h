@@ -363,6 +363,106 @@ void hdmc_batch_destroy(hdmc_batch_t *b);
 int hdmc_histogram_noalloc(const double *dev_local, int32_t mx, int32_t my, double wx, double wy, double sigma,
                            int32_t nbins, double dr, uint64_t *hist, void *stream);
 
+/* ---- three dimensions: hard spheres ----------------------------------------
+ * The same method for N hard spheres of diameter sigma in a periodic
+ * Lx x Ly x Lz box (the paper gives the 3-d case in words: eight
+ * checkerboard sets, eight sub-sweeps per sweep, Sec. 2.1, 2.2 and 6):
+ *   - cells: m_a = largest even integer <= L_a/sigma per axis (>= 4), widths
+ *     w_a = L_a/m_a with wx^2 + wy^2 + wz^2 < 4 sigma^2, so that a cell holds
+ *     at most HDMC3_SLOTS = 8 centres (each of its eight half-size boxes is
+ *     less than sigma across); mx*my*mz < 2^32;
+ *   - set Q = (cx mod 2) + 2 (cy mod 2) + 4 (cz mod 2); a sweep draws the
+ *     order of the eight sets (Fisher-Yates) and a shift direction among
+ *     +-x, +-y, +-z with a distance uniform in [0, w/2);
+ *   - a cell update shuffles its spheres and makes n_M trial moves, each a
+ *     displacement uniform in the ball of radius d, rejected when it leaves
+ *     the cell or overlaps a sphere of the 27-cell neighbourhood;
+ *   - pressure from the contact value, beta P / rho = 1 + (2 pi/3) rho
+ *     sigma^3 g(sigma+), g(R_i) from spherical shells.
+ * Conventions (return codes, host pointers, stream, synchronisation) are
+ * those of the two-dimensional entry points above.  Canonical layout: cell
+ * c = (cz*my + cy)*mx + cx, slot j, coordinate a (0 x, 1 y, 2 z) of a sphere
+ * at local[(8c+j)*3 + a], relative to the cell's lower corner, in [0, w_a);
+ * slot j is used iff j < counts[c]; unused slots read HDMC_EMPTY_SLOT. */
+typedef struct hdmc3_handle hdmc3_t;
+#define HDMC3_SLOTS 8
+
+/* Creates a system.  xyz: NULL for the face-centred cubic start (N = 4 q^3;
+ * site p = 4((k q + j) q + i) + s at ((b + s + 1/4) L_a/q) for unit cell
+ * b = (i,j,k) and basis vector s in {(0,0,0), (1/2,1/2,0), (1/2,0,1/2),
+ * (0,1/2,1/2)}, displaced uniformly within 0.01 sigma), else host global
+ * coordinates xyz[3i + a] in [0, L_a] (slot order = order of i within a
+ * cell).  d: maximum displacement, 0 < d < min(w)/2; nselect: n_M, 1..255;
+ * precision: HDMC_FP64 or HDMC_FP32_LOCAL (binary32 cell-local offsets).
+ * stream: cudaStream_t or NULL.  Device memory (two copies of the cells,
+ * 8 slots x 3 coordinates per cell, plus a few kilobytes) is allocated with
+ * cudaMalloc and freed by hdmc3_destroy.  Errors: HDMC_EINVAL, HDMC_EOVERLAP,
+ * HDMC_EOVERFLOW, HDMC_ENOMEM, HDMC_ECUDA; *out is NULL on failure.
+ * Synchronises. */
+int hdmc3_create(hdmc3_t **out, int64_t N, double Lx, double Ly, double Lz, double sigma, double d,
+                 int nselect, uint64_t seed, int precision, const double *xyz, void *stream);
+
+/* Enqueues n sweeps: one launch of the sweep draws per 64 sweeps, then per
+ * sweep eight sub-sweep launches and one cell-shift launch. */
+int hdmc3_sweep(hdmc3_t *h, int64_t n);
+
+/* Enqueues one extra cell shift drawn from the stream of explicit shifts. */
+int hdmc3_shift(hdmc3_t *h);
+
+/* Enqueues one sub-sweep of set Q (0..7) with the cell streams of sweep
+ * index `sweep` (a test hook: a sweep is eight of these and a shift). */
+int hdmc3_subsweep(hdmc3_t *h, uint32_t sweep, int Q);
+
+/* Enqueues the contact histogram (ordered pairs at distance in
+ * [sigma, 1.02 sigma), bins of 1e-4 sigma, decided in binary64 over the
+ * 5x5x5 cell neighbourhood) and adds it to the sample accumulator. */
+int hdmc3_sample(hdmc3_t *h);
+
+/* Pressure from the accumulated samples (one sample of the current
+ * configuration first if there is none): g(R_i) = n_i / (n_conf N rho
+ * (4 pi/3)(r_{i+1}^3 - r_i^3)) at R_i = (3/4)(r_{i+1}^4 - r_i^4) /
+ * (r_{i+1}^3 - r_i^3), the degree-5 least-squares polynomial over
+ * (sigma, 1.02 sigma] evaluated at sigma, beta P / rho = 1 + (2 pi/3) rho
+ * sigma^3 g(sigma+).  Outputs nullable as in hdmc_pressure.  Clears the
+ * accumulator.  Synchronises. */
+int hdmc3_pressure(hdmc3_t *h, double *betaP_over_rho, double *g_contact, uint64_t *hist, int64_t *n_samples);
+
+/* Global coordinates into host xyz[3N] in canonical (cell, slot) order:
+ * O_a + (c_a w_a + local_a) wrapped into [0, m_a w_a) (binary32 widths in
+ * HDMC_FP32_LOCAL mode).  Synchronises. */
+int hdmc3_positions(hdmc3_t *h, double *xyz);
+
+/* Raw state in the canonical layout: local (host, 24 C doubles), counts
+ * (host, C bytes), C = mx*my*mz.  Synchronises. */
+int hdmc3_get_state(hdmc3_t *h, double *local, uint8_t *counts);
+
+/* Cumulative trial counters as hdmc_counters.  Synchronises. */
+int hdmc3_counters(hdmc3_t *h, uint64_t out[4]);
+
+/* Grid m[3], widths w[3] (binary64), origin[3], sweeps and explicit shifts
+ * done (each nullable).  Synchronises. */
+int hdmc3_info(hdmc3_t *h, int32_t m[3], double w[3], double origin[3], uint64_t *sweeps_done,
+               uint64_t *shifts_done);
+
+/* Maximum displacement for the sweeps enqueued after the call
+ * (0 < d < min(w)/2). */
+int hdmc3_set_move_size(hdmc3_t *h, double d);
+
+/* Balance controls as hdmc_set_balance (shuffle_sets = 0 takes the sets in
+ * the order 0..7). */
+int hdmc3_set_balance(hdmc3_t *h, int shuffle_particles, int shuffle_sets);
+
+/* Waits for the handle's stream and reports device-side errors. */
+int hdmc3_sync(hdmc3_t *h);
+
+/* Profiling form of hdmc3_sweep: n sweeps with the same results, an event
+ * pair around every launch; mean milliseconds of one sub-sweep launch and
+ * one shift launch (nullable).  Synchronises. */
+int hdmc3_profile_sweeps(hdmc3_t *h, int64_t n, double *ms_subsweep, double *ms_shift);
+
+/* Frees the handle. */
+void hdmc3_destroy(hdmc3_t *h);
+
 /* Frees the handle (and the workspace if the library allocated it). */
 void hdmc_destroy(hdmc_t *h);
 

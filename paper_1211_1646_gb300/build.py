@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhdmc.so")
 SOURCES = ["hdmc_api.cu", "hdmc_host.cu", "hdmc_batch.cu", "hdmc_draws.cu", "hdmc_f32.cu", "hdmc_f64.cu",
-           "hdmc_noalloc.cu"]
+           "hdmc_noalloc.cu", "hdmc3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -1,0 +1,1189 @@
+// hdmc3.cu -- the method in three dimensions: hard spheres in cubic cells,
+// eight checkerboard sets (the paper describes the 3-d case in words:
+// Sec. 2.1 and 2.2 give eight sets and eight sub-sweeps per sweep, Sec. 6
+// discusses hard spheres).  Kernels and host entry points of the hdmc3_*
+// part of the C ABI.
+//
+// Device layout: the cells of one set are contiguous (set-major), row-major
+// over the half-resolution grid within a set, as in two dimensions.  A cell
+// holds 8 slots x 3 coordinates as x0..x7, y0..y7, z0..z7 (96 bytes in
+// binary32, 192 in binary64); slots are filled from slot 0, an unused slot
+// reads kEmpty.
+//
+// Random streams (Philox4x32-10 keyed by the seed), with c the canonical cell
+// number (cz*my + cy)*mx + cx:
+//   sweep draws of sweep s:          (s, 0xFFFFFFFF, 2<<28): Fisher-Yates
+//                                    order of the 8 sets, direction f in 0..5,
+//                                    distance unif53 * w/2
+//   explicit shift k:                (k, 0xFFFFFFFF, 4<<28): f, distance
+//   shuffle of cell c, sweep s, Q:   (s, c, (0<<28)|(Q<<24)): k in [0, n!)
+//   trials of that update:           (s, c, (1<<28)|(Q<<24)): consecutive
+//                                    words, six per attempt (three sym52),
+//                                    kept inside the unit ball
+//   start jitter of sphere p:        (p, 0xFFFFFFFE, 3<<28)
+//
+// Sub-sweep kernel: one thread per active cell.  Before its trials a thread
+// gathers, into shared memory, the spheres of its 26 neighbour cells that lie
+// within sigma (with a margin) of its cell's box: no other sphere can overlap
+// a trial position inside the cell, so the decisions are those of testing the
+// whole neighbourhood, and every test keeps the arithmetic of the serial form.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hdmc.h"
+#include "hdmc_device.cuh"
+
+namespace hdmc {
+
+// Host helpers of the two-dimensional entry points (hdmc_host.cu).
+int cuda_code(cudaError_t e);
+void bin_axis(double x, double w, int m, int& cell, double& loc);
+double poly_intercept(const std::vector<double>& t, const std::vector<double>& y, int deg);
+void squared_edges(double sigma, double* E);
+
+constexpr int kSlots3 = 8;          // sum of w^2 < 4 sigma^2 => at most 8 centres per cell
+constexpr int kCell3 = 3 * kSlots3;  // coordinates per cell
+constexpr int kSubB3 = 64;          // sub-sweep block: 64 active cells
+constexpr int kCand3 = 28;          // gathered neighbour spheres per cell (more: read from global)
+constexpr int kShiftB3 = 256;
+constexpr int kHistB3 = 128;
+constexpr int kDrawChunk3 = 64;     // sweeps per draws launch
+
+struct G3 {
+    int m[3];              // cells per axis (even)
+    int h[3];              // m/2
+    unsigned cq;           // cells per set
+    unsigned C;            // all cells
+    double w[3];           // widths, binary64
+    float wf[3];           // binary32 widths
+    double wprev[3];       // largest binary64 below w
+    float wprevf[3];       // largest binary32 below wf
+    double sigma, sig2;
+    float sig2f;
+    float keep2f;          // gather threshold sigma^2 (1 + 1e-3), binary32
+    float band_lo, band_hi;   // sigma^2 (1 -+ 2^-14): binary32 pair tests outside decide (binary64 mode)
+    double d;
+    float df;
+    int nsel;
+    uint32_t key0, key1;
+    uint32_t flags;        // kNoParticleShuffle | kNoSetShuffle
+};
+
+struct alignas(8) Draw3 {
+    uint32_t sweep;        // counter word 0 of the cell streams
+    int32_t fdir;          // 2*axis + (1 for the negative direction)
+    uint8_t perm[8];       // set of sub-sweep k
+    double ds;
+};
+
+struct Dev3 {
+    unsigned long long ctr[4];   // trials, accepted, left the cell, overlap
+    double origin[3];
+    unsigned int error;          // bit 0: a cell received more than 8 spheres
+    unsigned int pad;
+};
+
+__host__ __device__ inline unsigned sidx3(const G3& g, int cx, int cy, int cz) {
+    const unsigned q = (unsigned)((cx & 1) + 2 * (cy & 1) + 4 * (cz & 1));
+    return q * g.cq + ((unsigned)(cz >> 1) * (unsigned)g.h[1] + (unsigned)(cy >> 1)) * (unsigned)g.h[0] +
+           (unsigned)(cx >> 1);
+}
+
+__device__ __forceinline__ uint32_t factorial8(int n) {
+    uint32_t f = 1;
+#pragma unroll
+    for (int k = 2; k <= 8; ++k) f = k <= n ? f * (uint32_t)k : f;
+    return f;
+}
+
+// Precision-specific arithmetic; each form is the one the serial reference
+// evaluates (binary64: plain operations; binary32: fma where it writes fma).
+template <typename T> struct Ar3;
+template <> struct Ar3<double> {
+    __device__ static double w(const G3& g, int a) { return g.w[a]; }
+    __device__ static double trial(const G3& g, double x, double u) { return x + g.d * u; }
+    __device__ static bool hit(const G3& g, double dx, double dy, double dz) {
+        return (dx * dx + dy * dy) + dz * dz < g.sig2;
+    }
+};
+template <> struct Ar3<float> {
+    __device__ static float w(const G3& g, int a) { return g.wf[a]; }
+    __device__ static float trial(const G3& g, float x, float u) { return fmaf(g.df, u, x); }
+    __device__ static bool hit(const G3& g, float dx, float dy, float dz) {
+        return fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, -g.sig2f))) < 0.0f;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T pick8(const T (&v)[8], int i) {
+    T r = v[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) r = i == j ? v[j] : r;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void put8(T (&v)[8], int i, T x) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = i == j ? x : v[j];
+}
+
+// Swap slots J and r (r <= J) of the three coordinate arrays.
+template <int J, typename T>
+__device__ __forceinline__ void swap_slot3(T (&x)[8], T (&y)[8], T (&z)[8], int r) {
+    const T ax = pick8(x, r), ay = pick8(y, r), az = pick8(z, r);
+#pragma unroll
+    for (int s = 0; s < J; ++s) {
+        x[s] = s == r ? x[J] : x[s];
+        y[s] = s == r ? y[J] : y[s];
+        z[s] = s == r ? z[J] : z[s];
+    }
+    x[J] = ax;
+    y[J] = ay;
+    z[J] = az;
+}
+
+// Fisher-Yates decode of k in [0, n!): for j = n-1 down to 1 swap slots j and
+// k mod (j+1), then k /= (j+1).
+template <typename T>
+__device__ __forceinline__ void shuffle3(T (&x)[8], T (&y)[8], T (&z)[8], int n, uint32_t k) {
+#define HDMC3_STEP(J)                                        \
+    if (J < n) {                                             \
+        const int r = (int)(k % (uint32_t)(J + 1));          \
+        k /= (uint32_t)(J + 1);                              \
+        swap_slot3<J>(x, y, z, r);                           \
+    }
+    HDMC3_STEP(7) HDMC3_STEP(6) HDMC3_STEP(5) HDMC3_STEP(4) HDMC3_STEP(3) HDMC3_STEP(2) HDMC3_STEP(1)
+#undef HDMC3_STEP
+}
+
+__device__ __forceinline__ int wrap3(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
+
+// 256-bit loads and stores of one coordinate part (8 slots) of a cell.
+__device__ __forceinline__ void ld_part(const float* p, float (&v)[8]) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+__device__ __forceinline__ void ld_part(const double* p, double (&v)[8]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = q[i];
+        v[2 * i] = a.x;
+        v[2 * i + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void st_part(float* p, const float (&v)[8]) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void st_part(double* p, const double (&v)[8]) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+template <typename T>
+__device__ __forceinline__ void ld_cell3(const T* p, T (&x)[8], T (&y)[8], T (&z)[8]) {
+    ld_part(p, x);
+    ld_part(p + 8, y);
+    ld_part(p + 16, z);
+}
+template <typename T>
+__device__ __forceinline__ void st_cell3(T* p, const T (&x)[8], const T (&y)[8], const T (&z)[8]) {
+    st_part(p, x);
+    st_part(p + 8, y);
+    st_part(p + 16, z);
+}
+
+// Is (hi:lo, ...) an attempt inside the unit ball?  The definition is the
+// binary64 test (u0*u0 + u1*u1) + u2*u2 < 1 on the three sym52 variates.  A
+// binary32 estimate from the high words (each within 6.1e-8 of its variate,
+// so the estimate of the sum within 1e-6) decides whenever it lies farther
+// than 2^-16 from 1; the rest are decided in binary64.
+__device__ __forceinline__ bool inside_ball(const uint32_t (&w)[6]) {
+    const float a = (float)(int32_t)(w[0] ^ 0x80000000u) * 0x1p-31f;
+    const float b = (float)(int32_t)(w[2] ^ 0x80000000u) * 0x1p-31f;
+    const float c = (float)(int32_t)(w[4] ^ 0x80000000u) * 0x1p-31f;
+    const float s = a * a + b * b + c * c;
+    if (s < 1.0f - 0x1p-16f) return true;
+    if (s > 1.0f + 0x1p-16f) return false;
+    const double u0 = sym52(w[0], w[1]), u1 = sym52(w[2], w[3]), u2 = sym52(w[4], w[5]);
+    return (u0 * u0 + u1 * u1) + u2 * u2 < 1.0;
+}
+
+// binary32 rounding of sym52(hi, lo) = m 2^-52, m = 2k + 1 - 2^52: rounding
+// commutes with the power-of-two scale, so it is the rounded integer m
+// times 2^-52.
+__device__ __forceinline__ float sym52_f32(uint32_t hi, uint32_t lo) {
+    const uint64_t k = (((uint64_t)hi << 32) | lo) >> 12;
+    const long long m = (long long)(2 * k + 1) - (1LL << 52);
+    return __ll2float_rn(m) * 0x1p-52f;
+}
+
+template <typename T> struct Dir3;
+template <> struct Dir3<float> {
+    __device__ static float get(uint32_t hi, uint32_t lo) { return sym52_f32(hi, lo); }
+};
+template <> struct Dir3<double> {
+    __device__ static double get(uint32_t hi, uint32_t lo) { return sym52(hi, lo); }
+};
+
+// Pair test on binary32 copies of the coordinates: 1 overlap, 0 none, 2 too
+// close to contact for binary32 to decide (binary64 only; the copies are
+// within 3e-7 of the binary64 values, so r^2 is within 1e-5 of the binary64
+// one, well inside the 2^-14 sigma^2 band).  In binary32 mode the copies are
+// the coordinates and this is the method's own test.
+template <typename T>
+__device__ __forceinline__ int quick_hit(const G3& g, float dx, float dy, float dz);
+template <>
+__device__ __forceinline__ int quick_hit<float>(const G3& g, float dx, float dy, float dz) {
+    return fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, -g.sig2f))) < 0.0f;
+}
+template <>
+__device__ __forceinline__ int quick_hit<double>(const G3& g, float dx, float dy, float dz) {
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    return r2 < g.band_lo ? 1 : (r2 > g.band_hi ? 0 : 2);
+}
+
+// Exact test of the trial position against every sphere of the neighbour
+// cell with storage index sn (its offset from the cell (cx,cy,cz) is
+// recovered from the grid: m >= 4 makes it unique).
+template <typename T>
+__device__ bool cell_hit_exact(const G3& g, const T* cells, unsigned sn, int cx, int cy, int cz, T px, T py, T pz) {
+    using A = Ar3<T>;
+    const unsigned Q = sn / g.cq, r0 = sn % g.cq;
+    const int ix = (int)(r0 % (unsigned)g.h[0]);
+    const unsigned r1 = r0 / (unsigned)g.h[0];
+    const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
+    int dd[3] = {2 * ix + (int)(Q & 1) - cx, 2 * iy + (int)((Q >> 1) & 1) - cy, 2 * iz + (int)(Q >> 2) - cz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dd[a] = dd[a] > 1 ? dd[a] - g.m[a] : (dd[a] < -1 ? dd[a] + g.m[a] : dd[a]);
+    const T* nb = cells + (size_t)sn * kCell3;
+    const T sx = (T)dd[0] * A::w(g, 0), sy = (T)dd[1] * A::w(g, 1), sz = (T)dd[2] * A::w(g, 2);
+    bool hit = false;
+    for (int j = 0; j < kSlots3; ++j) {
+        const T qx = nb[j];
+        if (qx == (T)kEmpty) break;
+        hit |= A::hit(g, px - (qx + sx), py - (nb[8 + j] + sy), pz - (nb[16 + j] + sz));
+    }
+    return hit;
+}
+
+// Does the trial position hit a sphere of the 26 neighbour cells?  Reads
+// global memory (used when a cell has more than kCand3 gathered spheres).
+template <typename T>
+__device__ bool neighbour_hit_global(const G3& g, const T* cells, int cx, int cy, int cz, T px, T py, T pz) {
+    using A = Ar3<T>;
+    bool hit = false;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const T* nb = cells + (size_t)sidx3(g, wrap3(cx + dx, g.m[0]), wrap3(cy + dy, g.m[1]),
+                                                    wrap3(cz + dz, g.m[2])) * kCell3;
+                const T sx = (T)dx * A::w(g, 0), sy = (T)dy * A::w(g, 1), sz = (T)dz * A::w(g, 2);
+                for (int j = 0; j < kSlots3; ++j) {
+                    const T qx = nb[j];
+                    if (qx == (T)kEmpty) break;
+                    const T ex = qx + sx, ey = nb[8 + j] + sy, ez = nb[16 + j] + sz;
+                    hit |= A::hit(g, px - ex, py - ey, pz - ez);
+                }
+            }
+    return hit;
+}
+
+// Gather the occupied slots of one neighbour cell (offset dx,dy,dz, storage
+// index sn) that lie within reach of the active cell [0,w)^3: their binary32
+// image coordinates, and sn, go to the thread's candidate list.
+template <typename T>
+__device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const T (&qy)[8], const T (&qz)[8],
+                                            int dx, int dy, int dz, unsigned sn, float4 (*cand)[kSubB3], int& nc) {
+    const float w0 = g.wf[0], w1 = g.wf[1], w2 = g.wf[2];
+    const float sx = (float)dx * w0, sy = (float)dy * w1, sz = (float)dz * w2;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (qx[j] != (T)kEmpty) {
+            const float ex = (float)qx[j] + sx, ey = (float)qy[j] + sy, ez = (float)qz[j] + sz;
+            const float gx = ex < 0.0f ? -ex : (ex > w0 ? ex - w0 : 0.0f);
+            const float gy = ey < 0.0f ? -ey : (ey > w1 ? ey - w1 : 0.0f);
+            const float gz = ez < 0.0f ? -ez : (ez > w2 ? ez - w2 : 0.0f);
+            if (gx * gx + gy * gy + gz * gz < g.keep2f) {
+                if (nc < kCand3) cand[nc][threadIdx.x] = make_float4(ex, ey, ez, __uint_as_float(sn));
+                ++nc;
+            }
+        }
+    }
+}
+
+// One sub-sweep: every cell of set Q = table[jd].perm[k] (Alg. 1, Alg. 2).
+// binary32: the neighbour cells of one x-row are loaded together (256-bit
+// loads) before they are scanned; binary64: one cell at a time.
+template <typename T>
+__global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, const Draw3* __restrict__ table,
+                                                 int jd, int k, Dev3* st) {
+    using A = Ar3<T>;
+    __shared__ float4 cand[kCand3][kSubB3];
+    const Draw3& dr = table[jd];
+    const int Q = dr.perm[k];
+    const unsigned s = blockIdx.x * kSubB3 + threadIdx.x;
+    uint32_t n_tr = 0, n_ac = 0, n_lf = 0, n_ov = 0;
+    if (s < g.cq) {
+        const int ix = (int)(s % (unsigned)g.h[0]);
+        const unsigned r = s / (unsigned)g.h[0];
+        const int iy = (int)(r % (unsigned)g.h[1]);
+        const int iz = (int)(r / (unsigned)g.h[1]);
+        const int cx = 2 * ix + (Q & 1), cy = 2 * iy + ((Q >> 1) & 1), cz = 2 * iz + (Q >> 2);
+        T* own = cells + ((size_t)Q * g.cq + s) * kCell3;
+        T x[8], y[8], z[8];
+        ld_cell3(own, x, y, z);
+        int n = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) n += x[j] != (T)kEmpty;
+        if (n > 0) {
+            const uint32_t c = ((uint32_t)cz * (uint32_t)g.m[1] + (uint32_t)cy) * (uint32_t)g.m[0] + (uint32_t)cx;
+            const uint32_t setbits = (uint32_t)Q << 24;
+            if (n >= 2 && !(g.flags & kNoParticleShuffle)) {
+                WordStream S(g.key0, g.key1, dr.sweep, c, (kDomShuffle << 28) | setbits);
+                shuffle3(x, y, z, n, S.bounded(factorial8(n)));
+            }
+            int nc = 0;
+#pragma unroll 1
+            for (int row = 0; row < 9; ++row) {
+                const int dz = row / 3 - 1, dy = row % 3 - 1;
+                const int ny = wrap3(cy + dy, g.m[1]), nz = wrap3(cz + dz, g.m[2]);
+                if (sizeof(T) == 4) {
+                    T ax[3][8], ay[3][8], az[3][8];
+                    unsigned sn[3];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        sn[e] = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
+                        ld_cell3(cells + (size_t)sn[e] * kCell3, ax[e], ay[e], az[e]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 3; ++e)
+                        if (e != 1 || row != 4) gather_cell(g, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], cand, nc);
+                } else {
+#pragma unroll 1
+                    for (int e = 0; e < 3; ++e) {
+                        if (e == 1 && row == 4) continue;
+                        const unsigned sn = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
+                        T ax[8], ay[8], az[8];
+                        ld_cell3(cells + (size_t)sn * kCell3, ax, ay, az);
+                        gather_cell(g, ax, ay, az, e - 1, dy, dz, sn, cand, nc);
+                    }
+                }
+            }
+            const bool spill = nc > kCand3;
+            float fx[8], fy[8], fz[8];   // binary32 copies of the own coordinates
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                fx[j] = (float)x[j];
+                fy[j] = (float)y[j];
+                fz[j] = (float)z[j];
+            }
+            const T w0 = A::w(g, 0), w1 = A::w(g, 1), w2 = A::w(g, 2);
+            WordStream TS(g.key0, g.key1, dr.sweep, c, (kDomTrial << 28) | setbits);
+            int i = 0;
+            for (int t = 0; t < g.nsel; ++t) {
+                uint32_t wd[6];
+                for (;;) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) wd[q] = TS.next();
+                    if (inside_ball(wd)) break;
+                }
+                const T px = A::trial(g, pick8(x, i), Dir3<T>::get(wd[0], wd[1]));
+                const T py = A::trial(g, pick8(y, i), Dir3<T>::get(wd[2], wd[3]));
+                const T pz = A::trial(g, pick8(z, i), Dir3<T>::get(wd[4], wd[5]));
+                ++n_tr;
+                if (!(px >= (T)0 && px < w0 && py >= (T)0 && py < w1 && pz >= (T)0 && pz < w2)) {
+                    ++n_lf;
+                } else {
+                    const float pfx = (float)px, pfy = (float)py, pfz = (float)pz;
+                    bool hit = false;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < n && j != i) {
+                            int h = quick_hit<T>(g, pfx - fx[j], pfy - fy[j], pfz - fz[j]);
+                            if (h == 2) h = A::hit(g, px - x[j], py - y[j], pz - z[j]);
+                            hit |= h != 0;
+                        }
+                    if (!spill) {
+                        for (int q = 0; q < nc && !hit; ++q) {
+                            const float4 e = cand[q][threadIdx.x];
+                            int h = quick_hit<T>(g, pfx - e.x, pfy - e.y, pfz - e.z);
+                            if (h == 2) h = cell_hit_exact(g, cells, __float_as_uint(e.w), cx, cy, cz, px, py, pz);
+                            hit = h != 0;
+                        }
+                    } else if (!hit) {
+                        hit = neighbour_hit_global(g, cells, cx, cy, cz, px, py, pz);
+                    }
+                    if (hit) {
+                        ++n_ov;
+                    } else {
+                        put8(x, i, px);
+                        put8(y, i, py);
+                        put8(z, i, pz);
+                        put8(fx, i, pfx);
+                        put8(fy, i, pfy);
+                        put8(fz, i, pfz);
+                        ++n_ac;
+                    }
+                }
+                i = i + 1 == n ? 0 : i + 1;
+            }
+            st_cell3(own, x, y, z);
+        }
+    }
+    const unsigned a = __reduce_add_sync(0xFFFFFFFFu, n_tr), b = __reduce_add_sync(0xFFFFFFFFu, n_ac);
+    const unsigned cc = __reduce_add_sync(0xFFFFFFFFu, n_lf), d = __reduce_add_sync(0xFFFFFFFFu, n_ov);
+    if ((threadIdx.x & 31) == 0 && a) {
+        atomicAdd(&st->ctr[0], (unsigned long long)a);
+        atomicAdd(&st->ctr[1], (unsigned long long)b);
+        atomicAdd(&st->ctr[2], (unsigned long long)cc);
+        atomicAdd(&st->ctr[3], (unsigned long long)d);
+    }
+}
+
+// Sweep or shift draws for `count` consecutive indices starting at `first`.
+__global__ void k_draws3(G3 g, Draw3* table, uint32_t first, int count, int sweep_mode) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t index = first + (uint32_t)i;
+    WordStream s(g.key0, g.key1, index, 0xFFFFFFFFu, (sweep_mode ? kDomSweep : kDomShift) << 28);
+    int p[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+    if (sweep_mode) {
+#pragma unroll
+        for (int j = 7; j >= 1; --j) {
+            const int k = (int)s.bounded((uint32_t)(j + 1));
+            const int t = p[j];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q == k) {
+                    p[j] = p[q];
+                    p[q] = t;
+                }
+        }
+    }
+    Draw3 r;
+    const bool fixed = (g.flags & kNoSetShuffle) != 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r.perm[q] = (uint8_t)(fixed ? q : p[q]);
+    r.fdir = (int32_t)s.bounded(6u);
+    const uint32_t hi = s.next();
+    const uint32_t lo = s.next();
+    const int ax = r.fdir >> 1;
+    const double w = ax == 0 ? g.w[0] : (ax == 1 ? g.w[1] : g.w[2]);
+    r.ds = unif53(hi, lo) * (0.5 * w);
+    r.sweep = index;
+    table[i] = r;
+}
+
+// Cell shift (Alg. 4) along one of three axes: new cell c keeps the spheres
+// of old c that stay inside it (slot order), then takes those of old c+f
+// that leave c+f, re-expressed in c's frame and clamped into [0, w).  Both
+// old cells are read with 256-bit loads and the new cell is put together in
+// registers.
+template <typename T>
+__device__ __forceinline__ T sel3(int ax, T a, T b, T c) {
+    return ax == 0 ? a : (ax == 1 ? b : c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__ src, T* __restrict__ dst,
+                                                     const Draw3* __restrict__ table, int jd, Dev3* st) {
+    const unsigned s = blockIdx.x * kShiftB3 + threadIdx.x;
+    if (s >= g.C) return;
+    const Draw3& dr = table[jd];
+    const int ax = dr.fdir >> 1;
+    const int sgn = (dr.fdir & 1) ? -1 : 1;
+    const unsigned Q = s / g.cq, r0 = s % g.cq;
+    const int ix = (int)(r0 % (unsigned)g.h[0]);
+    const unsigned r1 = r0 / (unsigned)g.h[0];
+    const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
+    int nx = 2 * ix + (int)(Q & 1), ny = 2 * iy + (int)((Q >> 1) & 1), nz = 2 * iz + (int)(Q >> 2);
+    if (ax == 0) nx = wrap3(nx + sgn, g.m[0]);
+    else if (ax == 1) ny = wrap3(ny + sgn, g.m[1]);
+    else nz = wrap3(nz + sgn, g.m[2]);
+    T ox[8], oy[8], oz[8], bx[8], by[8], bz[8];
+    ld_cell3(src + (size_t)s * kCell3, ox, oy, oz);
+    ld_cell3(src + (size_t)sidx3(g, nx, ny, nz) * kCell3, bx, by, bz);
+    T w, sd, sw, wprev;
+    if (sizeof(T) == 8) {
+        w = (T)g.w[ax];
+        sd = (T)((double)sgn * dr.ds);
+        sw = (T)((double)sgn * g.w[ax]);
+        wprev = (T)g.wprev[ax];
+    } else {
+        w = (T)g.wf[ax];
+        sd = (T)((float)sgn * (float)dr.ds);
+        sw = (T)((float)sgn * g.wf[ax]);
+        wprev = (T)g.wprevf[ax];
+    }
+    T rx[8], ry[8], rz[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) rx[j] = ry[j] = rz[j] = (T)kEmpty;
+    int k = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const T dp = sel3(ax, ox[j], oy[j], oz[j]) - sd;
+        if (ox[j] != (T)kEmpty && dp >= (T)0 && dp < w) {
+            put8(rx, k, ax == 0 ? dp : ox[j]);
+            put8(ry, k, ax == 1 ? dp : oy[j]);
+            put8(rz, k, ax == 2 ? dp : oz[j]);
+            ++k;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const T dp = sel3(ax, bx[j], by[j], bz[j]) - sd;
+        if (bx[j] != (T)kEmpty && !(dp >= (T)0 && dp < w)) {
+            T v = dp + sw;
+            if (v >= w) v = wprev;
+            if (v < (T)0) v = (T)0;
+            put8(rx, k, ax == 0 ? v : bx[j]);
+            put8(ry, k, ax == 1 ? v : by[j]);
+            put8(rz, k, ax == 2 ? v : bz[j]);
+            ++k;
+        }
+    }
+    if (k > kSlots3) atomicOr(&st->error, 1u);
+    st_cell3(dst + (size_t)s * kCell3, rx, ry, rz);
+    if (s == 0) st->origin[ax] += (double)sd;
+}
+
+// Contact histogram: every sphere against the spheres of its 5x5x5 cell
+// neighbourhood; a binary32 estimate of r^2 with a wide margin skips pairs
+// far outside [sigma^2, (sigma + 200 dr)^2), the rest are decided in binary64
+// on r^2 = (dx*dx + dy*dy) + dz*dz against the squared bin edges.
+template <typename T>
+__global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ cells,
+                                                   const double* __restrict__ edges2, float lo2f, float hi2f,
+                                                   unsigned long long* hist) {
+    __shared__ unsigned int sh[kHistBins];
+    for (int b = threadIdx.x; b < kHistBins; b += kHistB3) sh[b] = 0;
+    __syncthreads();
+    const unsigned s = blockIdx.x * kHistB3 + threadIdx.x;
+    if (s < g.C) {
+        const unsigned Q = s / g.cq, r0 = s % g.cq;
+        const int ix = (int)(r0 % (unsigned)g.h[0]);
+        const unsigned r1 = r0 / (unsigned)g.h[0];
+        const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
+        const int cx = 2 * ix + (int)(Q & 1), cy = 2 * iy + (int)((Q >> 1) & 1), cz = 2 * iz + (int)(Q >> 2);
+        const T* own = cells + (size_t)s * kCell3;
+        double w[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w[a] = sizeof(T) == 8 ? g.w[a] : (double)g.wf[a];
+        for (int i = 0; i < kSlots3; ++i) {
+            const T pxT = own[i];
+            if (pxT == (T)kEmpty) break;
+            const double px = (double)pxT, py = (double)own[8 + i], pz = (double)own[16 + i];
+            const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+            for (int dz = -2; dz <= 2; ++dz)
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        const int nx = ((cx + dx) % g.m[0] + g.m[0]) % g.m[0];
+                        const int ny = ((cy + dy) % g.m[1] + g.m[1]) % g.m[1];
+                        const int nz = ((cz + dz) % g.m[2] + g.m[2]) % g.m[2];
+                        const T* nb = cells + (size_t)sidx3(g, nx, ny, nz) * kCell3;
+                        const double sx = (double)dx * w[0], sy = (double)dy * w[1], sz = (double)dz * w[2];
+                        const float sxf = (float)sx, syf = (float)sy, szf = (float)sz;
+                        for (int j = 0; j < kSlots3; ++j) {
+                            const T qxT = nb[j];
+                            if (qxT == (T)kEmpty) break;
+                            if (dx == 0 && dy == 0 && dz == 0 && j == i) continue;
+                            const float fx = pxf - ((float)qxT + sxf), fy = pyf - ((float)nb[8 + j] + syf),
+                                        fz = pzf - ((float)nb[16 + j] + szf);
+                            const float r2f = fx * fx + fy * fy + fz * fz;
+                            if (r2f < lo2f || r2f > hi2f) continue;
+                            const double ex = px - ((double)qxT + sx), ey = py - ((double)nb[8 + j] + sy),
+                                         ez = pz - ((double)nb[16 + j] + sz);
+                            const double r2 = (ex * ex + ey * ey) + ez * ez;
+                            if (!(r2 >= edges2[0]) || !(r2 < edges2[kHistBins])) continue;
+                            int lo = 0, hi = kHistBins;   // largest b with edges2[b] <= r2
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (r2 >= edges2[mid]) lo = mid;
+                                else hi = mid;
+                            }
+                            atomicAdd(&sh[lo], 1u);
+                        }
+                    }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kHistBins; b += kHistB3)
+        if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
+}
+
+}  // namespace hdmc
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using namespace hdmc;
+
+struct hdmc3_handle {
+    G3 g;
+    int64_t N;
+    double L[3];
+    int prec;
+    cudaStream_t stream;
+    size_t el;                 // bytes per coordinate
+    void* cells[2];            // current state and shift target
+    int cur;
+    Draw3* table;              // kDrawChunk3 sweep draws + 1 extra entry
+    Dev3* st;
+    unsigned long long* hist;  // kHistBins accumulator
+    double* edges2;            // kHistBins + 1 squared bin edges
+    float lo2f, hi2f;
+    int64_t samples;
+    uint64_t sweeps, shifts;
+};
+
+namespace {
+
+int finish3(hdmc3_t* h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_code(e);
+    unsigned int err = 0;
+    e = cudaMemcpy(&err, &h->st->error, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_code(e);
+    return err ? HDMC_EOVERFLOW : HDMC_OK;
+}
+
+bool make_grid3(const double L[3], double sigma, int m[3], double w[3]) {
+    if (!(sigma > 0)) return false;
+    for (int a = 0; a < 3; ++a) {
+        if (!(L[a] > 0) || !std::isfinite(L[a])) return false;
+        const double q = std::floor(L[a] / sigma);
+        if (q > 2.0e9) return false;
+        m[a] = (int)q;
+        m[a] -= m[a] & 1;
+        if (m[a] < 4) return false;
+        w[a] = L[a] / m[a];
+    }
+    if ((int64_t)m[0] * m[1] * m[2] >= (int64_t(1) << 32)) return false;
+    return (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] < 4.0 * sigma * sigma;
+}
+
+// Face-centred cubic start (same definition as documented in hdmc.h).
+bool fcc_positions(int64_t N, const double L[3], double sigma, uint32_t k0, uint32_t k1, std::vector<double>& xyz) {
+    int64_t q = 1;
+    while (4 * q * q * q < N) ++q;
+    if (N < 4 || 4 * q * q * q != N) return false;
+    static const double basis[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    xyz.resize(3 * (size_t)N);
+    const double rj = 0.01 * sigma;
+    for (int64_t k = 0; k < q; ++k)
+        for (int64_t j = 0; j < q; ++j)
+            for (int64_t i = 0; i < q; ++i)
+                for (int s = 0; s < 4; ++s) {
+                    const int64_t p = 4 * ((k * q + j) * q + i) + s;
+                    const int64_t b[3] = {i, j, k};
+                    WordStream ws(k0, k1, (uint32_t)p, 0xFFFFFFFEu, kDomInit << 28);
+                    double u[3];
+                    for (;;) {
+                        for (int a = 0; a < 3; ++a) {
+                            const uint32_t hi = ws.next();
+                            const uint32_t lo = ws.next();
+                            u[a] = sym52(hi, lo);
+                        }
+                        if ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] < 1.0) break;
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        double x = ((double)b[a] + basis[s][a] + 0.25) * (L[a] / (double)q) + rj * u[a];
+                        if (x >= L[a]) x -= L[a];
+                        if (x < 0.0) x += L[a];
+                        xyz[3 * p + a] = x;
+                    }
+                }
+    return true;
+}
+
+// Canonical state (local[(8c+j)*3+a], cnt[c]) of global coordinates.
+int bin3(const hdmc3_t* h, const double* xyz, std::vector<double>& loc, std::vector<uint8_t>& cnt) {
+    const G3& g = h->g;
+    loc.assign((size_t)g.C * kCell3, kEmpty);
+    cnt.assign((size_t)g.C, 0);
+    for (int64_t p = 0; p < h->N; ++p) {
+        int cc[3];
+        double l[3];
+        for (int a = 0; a < 3; ++a) {
+            const double x = xyz[3 * p + a];
+            if (!(x >= 0.0 && x <= h->L[a])) return HDMC_EINVAL;
+            bin_axis(x, g.w[a], g.m[a], cc[a], l[a]);
+            if (h->prec == HDMC_FP32_LOCAL) {
+                float f = (float)l[a];
+                if (f >= g.wf[a]) f = g.wprevf[a];
+                l[a] = f;
+            }
+        }
+        const size_t c = ((size_t)cc[2] * g.m[1] + cc[1]) * g.m[0] + cc[0];
+        if (cnt[c] >= kSlots3) return HDMC_EOVERFLOW;
+        const int j = cnt[c]++;
+        for (int a = 0; a < 3; ++a) loc[(8 * c + j) * 3 + a] = l[a];
+    }
+    return HDMC_OK;
+}
+
+// Overlap test of every sphere against its 27-cell neighbourhood with the
+// arithmetic of the sweep.
+bool any_overlap3(const hdmc3_t* h, const std::vector<double>& loc, const std::vector<uint8_t>& cnt) {
+    const G3& g = h->g;
+    for (int cz = 0; cz < g.m[2]; ++cz)
+        for (int cy = 0; cy < g.m[1]; ++cy)
+            for (int cx = 0; cx < g.m[0]; ++cx) {
+                const size_t c = ((size_t)cz * g.m[1] + cy) * g.m[0] + cx;
+                for (int i = 0; i < cnt[c]; ++i)
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int n3[3] = {(cx + dx + g.m[0]) % g.m[0], (cy + dy + g.m[1]) % g.m[1],
+                                                   (cz + dz + g.m[2]) % g.m[2]};
+                                const int dd[3] = {dx, dy, dz};
+                                const size_t nc = ((size_t)n3[2] * g.m[1] + n3[1]) * g.m[0] + n3[0];
+                                for (int j = 0; j < cnt[nc]; ++j) {
+                                    if (dx == 0 && dy == 0 && dz == 0 && i == j) continue;
+                                    if (h->prec == HDMC_FP64) {
+                                        double e[3];
+                                        for (int a = 0; a < 3; ++a)
+                                            e[a] = loc[(8 * c + i) * 3 + a] -
+                                                   (loc[(8 * nc + j) * 3 + a] + (double)dd[a] * g.w[a]);
+                                        if ((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2] < g.sig2) return true;
+                                    } else {
+                                        float e[3];
+                                        for (int a = 0; a < 3; ++a)
+                                            e[a] = (float)loc[(8 * c + i) * 3 + a] -
+                                                   ((float)loc[(8 * nc + j) * 3 + a] + (float)dd[a] * g.wf[a]);
+                                        if (std::fma(e[0], e[0], std::fma(e[1], e[1], std::fma(e[2], e[2], -g.sig2f))) <
+                                            0.0f)
+                                            return true;
+                                    }
+                                }
+                            }
+            }
+    return false;
+}
+
+void pack3(const hdmc3_t* h, const std::vector<double>& loc, const std::vector<uint8_t>& cnt, std::vector<char>& raw) {
+    const G3& g = h->g;
+    raw.assign((size_t)g.C * kCell3 * h->el, 0);
+    for (int cz = 0; cz < g.m[2]; ++cz)
+        for (int cy = 0; cy < g.m[1]; ++cy)
+            for (int cx = 0; cx < g.m[0]; ++cx) {
+                const size_t c = ((size_t)cz * g.m[1] + cy) * g.m[0] + cx;
+                const size_t s = sidx3(g, cx, cy, cz);
+                for (int j = 0; j < kSlots3; ++j)
+                    for (int a = 0; a < 3; ++a) {
+                        const double v = j < cnt[c] ? loc[(8 * c + j) * 3 + a] : kEmpty;
+                        char* dst = raw.data() + (s * kCell3 + 8 * a + j) * h->el;
+                        if (h->prec == HDMC_FP64) std::memcpy(dst, &v, 8);
+                        else {
+                            const float f = (float)v;
+                            std::memcpy(dst, &f, 4);
+                        }
+                    }
+            }
+}
+
+void unpack3(const hdmc3_t* h, const std::vector<char>& raw, std::vector<double>& loc, std::vector<uint8_t>& cnt) {
+    const G3& g = h->g;
+    loc.assign((size_t)g.C * kCell3, kEmpty);
+    cnt.assign((size_t)g.C, 0);
+    for (int cz = 0; cz < g.m[2]; ++cz)
+        for (int cy = 0; cy < g.m[1]; ++cy)
+            for (int cx = 0; cx < g.m[0]; ++cx) {
+                const size_t c = ((size_t)cz * g.m[1] + cy) * g.m[0] + cx;
+                const size_t s = sidx3(g, cx, cy, cz);
+                int n = 0;
+                for (int j = 0; j < kSlots3; ++j) {
+                    double v[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const char* src = raw.data() + (s * kCell3 + 8 * a + j) * h->el;
+                        if (h->prec == HDMC_FP64) std::memcpy(&v[a], src, 8);
+                        else {
+                            float f;
+                            std::memcpy(&f, src, 4);
+                            v[a] = f;
+                        }
+                    }
+                    if (v[0] == kEmpty) continue;
+                    n = j + 1;
+                    for (int a = 0; a < 3; ++a) loc[(8 * c + j) * 3 + a] = v[a];
+                }
+                cnt[c] = (uint8_t)n;
+            }
+}
+
+int download3(hdmc3_t* h, std::vector<double>& loc, std::vector<uint8_t>& cnt) {
+    int e = finish3(h);
+    std::vector<char> raw((size_t)h->g.C * kCell3 * h->el);
+    const cudaError_t ce = cudaMemcpy(raw.data(), h->cells[h->cur], raw.size(), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_code(ce);
+    unpack3(h, raw, loc, cnt);
+    return e;
+}
+
+void launch_sub3(hdmc3_t* h, int jd, int k) {
+    const unsigned blocks = (h->g.cq + kSubB3 - 1) / kSubB3;
+    if (h->prec == HDMC_FP64)
+        k_sub3<double><<<blocks, kSubB3, 0, h->stream>>>(h->g, (double*)h->cells[h->cur], h->table, jd, k, h->st);
+    else
+        k_sub3<float><<<blocks, kSubB3, 0, h->stream>>>(h->g, (float*)h->cells[h->cur], h->table, jd, k, h->st);
+}
+
+void launch_shift3(hdmc3_t* h, int jd) {
+    const unsigned blocks = (h->g.C + kShiftB3 - 1) / kShiftB3;
+    if (h->prec == HDMC_FP64)
+        k_shift3<double><<<blocks, kShiftB3, 0, h->stream>>>(h->g, (const double*)h->cells[h->cur],
+                                                              (double*)h->cells[1 - h->cur], h->table, jd, h->st);
+    else
+        k_shift3<float><<<blocks, kShiftB3, 0, h->stream>>>(h->g, (const float*)h->cells[h->cur],
+                                                             (float*)h->cells[1 - h->cur], h->table, jd, h->st);
+    h->cur = 1 - h->cur;
+}
+
+void free3(hdmc3_t* h) {
+    if (!h) return;
+    cudaFree(h->cells[0]);
+    cudaFree(h->cells[1]);
+    cudaFree(h->table);
+    cudaFree(h->st);
+    cudaFree(h->hist);
+    cudaFree(h->edges2);
+    delete h;
+}
+
+// n sweeps; with events, the mean device time of the sub-sweep and shift
+// launches is measured.
+int enqueue_sweeps3(hdmc3_t* h, int64_t n, double* ms_sub, double* ms_shift) {
+    if (n < 0) return HDMC_EINVAL;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    auto mark = [&](int k) {
+        if (!ms_sub && !ms_shift) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, h->stream);
+        ev.push_back(e);
+        kind.push_back(k);
+    };
+    for (int64_t done = 0; done < n;) {
+        const int cnt = (int)std::min<int64_t>(kDrawChunk3, n - done);
+        k_draws3<<<1, kDrawChunk3, 0, h->stream>>>(h->g, h->table, (uint32_t)h->sweeps, cnt, 1);
+        for (int j = 0; j < cnt; ++j) {
+            for (int k = 0; k < 8; ++k) {
+                mark(0);
+                launch_sub3(h, j, k);
+                mark(-1);
+            }
+            mark(1);
+            launch_shift3(h, j);
+            mark(-1);
+            h->sweeps += 1;
+        }
+        done += cnt;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        for (auto x : ev) cudaEventDestroy(x);
+        return cuda_code(e);
+    }
+    if (!ev.empty()) {
+        cudaEventSynchronize(ev.back());
+        double tot[2] = {0, 0};
+        int num[2] = {0, 0};
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            tot[kind[i]] += ms;
+            num[kind[i]] += 1;
+        }
+        for (auto x : ev) cudaEventDestroy(x);
+        if (ms_sub) *ms_sub = num[0] ? tot[0] / num[0] : 0.0;
+        if (ms_shift) *ms_shift = num[1] ? tot[1] / num[1] : 0.0;
+    }
+    return HDMC_OK;
+}
+
+int set_geometry3(G3& g, const double L[3], double sigma, double d, int nselect, uint64_t seed) {
+    int m[3];
+    double w[3];
+    if (!make_grid3(L, sigma, m, w)) return HDMC_EINVAL;
+    if (nselect < 1 || nselect > 255) return HDMC_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(d > 0) || !(d < 0.5 * w[a])) return HDMC_EINVAL;
+    g = G3{};
+    for (int a = 0; a < 3; ++a) {
+        g.m[a] = m[a];
+        g.h[a] = m[a] / 2;
+        g.w[a] = w[a];
+        g.wf[a] = (float)w[a];
+        g.wprev[a] = std::nextafter(w[a], 0.0);
+        g.wprevf[a] = std::nextafter(g.wf[a], 0.0f);
+    }
+    g.cq = (unsigned)((int64_t)g.h[0] * g.h[1] * g.h[2]);
+    g.C = 8u * g.cq;
+    g.sigma = sigma;
+    g.sig2 = sigma * sigma;
+    g.sig2f = (float)(sigma * sigma);
+    g.keep2f = (float)(sigma * sigma * (1.0 + 1.0e-3));
+    g.band_lo = (float)(sigma * sigma * (1.0 - 0x1p-14));
+    g.band_hi = (float)(sigma * sigma * (1.0 + 0x1p-14));
+    g.d = d;
+    g.df = (float)d;
+    g.nsel = nselect;
+    g.key0 = (uint32_t)seed;
+    g.key1 = (uint32_t)(seed >> 32);
+    return HDMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hdmc3_create(hdmc3_t** out, int64_t N, double Lx, double Ly, double Lz, double sigma, double d, int nselect,
+                 uint64_t seed, int precision, const double* xyz, void* stream) {
+    if (!out) return HDMC_EINVAL;
+    *out = nullptr;
+    if (N < 1 || (precision != HDMC_FP64 && precision != HDMC_FP32_LOCAL)) return HDMC_EINVAL;
+    hdmc3_t* h = new hdmc3_t();
+    h->L[0] = Lx;
+    h->L[1] = Ly;
+    h->L[2] = Lz;
+    int e = set_geometry3(h->g, h->L, sigma, d, nselect, seed);
+    if (!e && (int64_t)h->g.C * kSlots3 < N) e = HDMC_EINVAL;
+    if (e) {
+        delete h;
+        return e;
+    }
+    h->N = N;
+    h->prec = precision;
+    h->el = precision == HDMC_FP64 ? 8 : 4;
+    h->stream = (cudaStream_t)stream;
+    std::vector<double> pos;
+    if (!xyz) {
+        if (!fcc_positions(N, h->L, sigma, h->g.key0, h->g.key1, pos)) {
+            delete h;
+            return HDMC_EINVAL;
+        }
+        xyz = pos.data();
+    }
+    std::vector<double> loc;
+    std::vector<uint8_t> cnt;
+    e = bin3(h, xyz, loc, cnt);
+    if (!e && any_overlap3(h, loc, cnt)) e = HDMC_EOVERLAP;
+    if (e) {
+        delete h;
+        return e;
+    }
+    std::vector<char> raw;
+    pack3(h, loc, cnt, raw);
+    const size_t bytes = raw.size();
+    cudaError_t ce = cudaMalloc(&h->cells[0], bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->cells[1], bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->table, sizeof(Draw3) * (kDrawChunk3 + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->st, sizeof(Dev3));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->hist, sizeof(unsigned long long) * kHistBins);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->edges2, sizeof(double) * (kHistBins + 1));
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->cells[0], raw.data(), bytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(h->st, 0, sizeof(Dev3));
+    if (ce == cudaSuccess) ce = cudaMemset(h->hist, 0, sizeof(unsigned long long) * kHistBins);
+    double E[kHistBins + 1];
+    squared_edges(sigma, E);
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->edges2, E, sizeof(E), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        free3(h);
+        return cuda_code(ce);
+    }
+    h->lo2f = (float)(E[0] * (1.0 - 1.0e-4));
+    h->hi2f = (float)(E[kHistBins] * (1.0 + 1.0e-4));
+    h->cur = 0;
+    *out = h;
+    return HDMC_OK;
+}
+
+int hdmc3_sweep(hdmc3_t* h, int64_t n) {
+    if (!h) return HDMC_EINVAL;
+    return enqueue_sweeps3(h, n, nullptr, nullptr);
+}
+
+int hdmc3_profile_sweeps(hdmc3_t* h, int64_t n, double* ms_subsweep, double* ms_shift) {
+    if (!h || n < 1) return HDMC_EINVAL;
+    double a = 0, b = 0;
+    int e = enqueue_sweeps3(h, n, &a, &b);
+    if (e) return e;
+    if (ms_subsweep) *ms_subsweep = a;
+    if (ms_shift) *ms_shift = b;
+    return finish3(h);
+}
+
+int hdmc3_shift(hdmc3_t* h) {
+    if (!h) return HDMC_EINVAL;
+    k_draws3<<<1, 1, 0, h->stream>>>(h->g, h->table + kDrawChunk3, (uint32_t)h->shifts, 1, 0);
+    launch_shift3(h, kDrawChunk3);
+    h->shifts += 1;
+    return cuda_code(cudaGetLastError());
+}
+
+int hdmc3_subsweep(hdmc3_t* h, uint32_t sweep, int Q) {
+    if (!h || Q < 0 || Q > 7) return HDMC_EINVAL;
+    Draw3 d{};
+    d.sweep = sweep;
+    for (int q = 0; q < 8; ++q) d.perm[q] = (uint8_t)q;
+    d.perm[0] = (uint8_t)Q;
+    cudaError_t e = cudaMemcpyAsync(h->table + kDrawChunk3, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_code(e);
+    e = cudaStreamSynchronize(h->stream);   // d lives on this stack frame
+    if (e != cudaSuccess) return cuda_code(e);
+    launch_sub3(h, kDrawChunk3, 0);
+    return cuda_code(cudaGetLastError());
+}
+
+int hdmc3_sample(hdmc3_t* h) {
+    if (!h) return HDMC_EINVAL;
+    const unsigned blocks = (h->g.C + kHistB3 - 1) / kHistB3;
+    if (h->prec == HDMC_FP64)
+        k_hist3<double><<<blocks, kHistB3, 0, h->stream>>>(h->g, (const double*)h->cells[h->cur], h->edges2,
+                                                            h->lo2f, h->hi2f, h->hist);
+    else
+        k_hist3<float><<<blocks, kHistB3, 0, h->stream>>>(h->g, (const float*)h->cells[h->cur], h->edges2,
+                                                           h->lo2f, h->hi2f, h->hist);
+    h->samples += 1;
+    return cuda_code(cudaGetLastError());
+}
+
+int hdmc3_pressure(hdmc3_t* h, double* betaP_over_rho, double* g_contact, uint64_t* hist, int64_t* n_samples) {
+    if (!h) return HDMC_EINVAL;
+    if (h->samples == 0) {
+        const int e = hdmc3_sample(h);
+        if (e) return e;
+    }
+    int e = finish3(h);
+    unsigned long long hh[kHistBins];
+    cudaError_t ce = cudaMemcpy(hh, h->hist, sizeof(hh), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemset(h->hist, 0, sizeof(hh));
+    if (ce != cudaSuccess) return cuda_code(ce);
+    const double sigma = h->g.sigma, dr = kHistDr * sigma, c = kFitRange * sigma;
+    const double rho = (double)h->N / (h->L[0] * h->L[1] * h->L[2]);
+    std::vector<double> t, gv;
+    for (int i = 0; i < kHistBins; ++i) {
+        const double r0 = sigma + dr * i, r1 = sigma + dr * (i + 1);
+        const double v0 = r0 * r0 * r0, v1 = r1 * r1 * r1;
+        const double R = 0.75 * (r1 * v1 - r0 * v0) / (v1 - v0);
+        if (!(R > sigma && R <= sigma + c)) continue;
+        t.push_back((R - sigma) / c);
+        gv.push_back((double)hh[i] / ((double)h->samples * (double)h->N * rho * (4.0 * M_PI / 3.0) * (v1 - v0)));
+    }
+    const double g0 = poly_intercept(t, gv, kFitDegree);
+    if (betaP_over_rho) *betaP_over_rho = 1.0 + (2.0 * M_PI / 3.0) * rho * sigma * sigma * sigma * g0;
+    if (g_contact) *g_contact = g0;
+    if (hist)
+        for (int i = 0; i < kHistBins; ++i) hist[i] = hh[i];
+    if (n_samples) *n_samples = h->samples;
+    h->samples = 0;
+    return e;
+}
+
+int hdmc3_get_state(hdmc3_t* h, double* local, uint8_t* counts) {
+    if (!h || !local || !counts) return HDMC_EINVAL;
+    std::vector<double> loc;
+    std::vector<uint8_t> cnt;
+    const int e = download3(h, loc, cnt);
+    if (e && e != HDMC_EOVERFLOW) return e;
+    std::memcpy(local, loc.data(), loc.size() * sizeof(double));
+    std::memcpy(counts, cnt.data(), cnt.size());
+    return e;
+}
+
+int hdmc3_positions(hdmc3_t* h, double* xyz) {
+    if (!h || !xyz) return HDMC_EINVAL;
+    std::vector<double> loc;
+    std::vector<uint8_t> cnt;
+    int e = download3(h, loc, cnt);
+    if (e && e != HDMC_EOVERFLOW) return e;
+    Dev3 st;
+    const cudaError_t ce = cudaMemcpy(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_code(ce);
+    const G3& g = h->g;
+    double w[3], L[3];
+    for (int a = 0; a < 3; ++a) {
+        w[a] = h->prec == HDMC_FP64 ? g.w[a] : (double)g.wf[a];
+        L[a] = h->prec == HDMC_FP64 ? h->L[a] : (double)g.m[a] * w[a];
+    }
+    int64_t p = 0;
+    for (int cz = 0; cz < g.m[2]; ++cz)
+        for (int cy = 0; cy < g.m[1]; ++cy)
+            for (int cx = 0; cx < g.m[0]; ++cx) {
+                const size_t c = ((size_t)cz * g.m[1] + cy) * g.m[0] + cx;
+                const int cc[3] = {cx, cy, cz};
+                for (int j = 0; j < cnt[c]; ++j) {
+                    if (p >= h->N) return HDMC_EOVERFLOW;
+                    for (int a = 0; a < 3; ++a) {
+                        const double gl = st.origin[a] + ((double)cc[a] * w[a] + loc[(8 * c + j) * 3 + a]);
+                        xyz[3 * p + a] = gl - L[a] * std::floor(gl / L[a]);
+                    }
+                    ++p;
+                }
+            }
+    return e;
+}
+
+int hdmc3_counters(hdmc3_t* h, uint64_t out[4]) {
+    if (!h || !out) return HDMC_EINVAL;
+    const int e = finish3(h);
+    Dev3 st;
+    const cudaError_t ce = cudaMemcpy(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_code(ce);
+    for (int k = 0; k < 4; ++k) out[k] = st.ctr[k];
+    return e;
+}
+
+int hdmc3_info(hdmc3_t* h, int32_t m[3], double w[3], double origin[3], uint64_t* sweeps_done,
+               uint64_t* shifts_done) {
+    if (!h) return HDMC_EINVAL;
+    const int e = finish3(h);
+    Dev3 st;
+    const cudaError_t ce = cudaMemcpy(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_code(ce);
+    for (int a = 0; a < 3; ++a) {
+        if (m) m[a] = h->g.m[a];
+        if (w) w[a] = h->g.w[a];
+        if (origin) origin[a] = st.origin[a];
+    }
+    if (sweeps_done) *sweeps_done = h->sweeps;
+    if (shifts_done) *shifts_done = h->shifts;
+    return e;
+}
+
+int hdmc3_set_move_size(hdmc3_t* h, double d) {
+    if (!h) return HDMC_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(d > 0) || !(d < 0.5 * h->g.w[a])) return HDMC_EINVAL;
+    h->g.d = d;
+    h->g.df = (float)d;
+    return HDMC_OK;
+}
+
+int hdmc3_set_balance(hdmc3_t* h, int shuffle_particles, int shuffle_sets) {
+    if (!h) return HDMC_EINVAL;
+    h->g.flags = (shuffle_particles ? 0u : kNoParticleShuffle) | (shuffle_sets ? 0u : kNoSetShuffle);
+    return HDMC_OK;
+}
+
+int hdmc3_sync(hdmc3_t* h) {
+    if (!h) return HDMC_EINVAL;
+    return finish3(h);
+}
+
+void hdmc3_destroy(hdmc3_t* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free3(h);
+}
+
+}  // extern "C"

@@ -80,6 +80,24 @@ SIGNATURES = {
     "hdmc_batch_destroy": (None, [_vp]),
     "hdmc_destroy": (None, [_vp]),
     "hdmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    # three dimensions
+    "hdmc3_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
+                                    ctypes.c_int, _f64p, _vp]),
+    "hdmc3_sweep": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "hdmc3_shift": (ctypes.c_int, [_vp]),
+    "hdmc3_subsweep": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_int]),
+    "hdmc3_sample": (ctypes.c_int, [_vp]),
+    "hdmc3_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
+    "hdmc3_positions": (ctypes.c_int, [_vp, _f64p]),
+    "hdmc3_get_state": (ctypes.c_int, [_vp, _f64p, _u8p]),
+    "hdmc3_counters": (ctypes.c_int, [_vp, _u64p]),
+    "hdmc3_info": (ctypes.c_int, [_vp, _i32p, _f64p, _f64p, _u64p, _u64p]),
+    "hdmc3_set_move_size": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "hdmc3_set_balance": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "hdmc3_sync": (ctypes.c_int, [_vp]),
+    "hdmc3_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
+    "hdmc3_destroy": (None, [_vp]),
 }
 
 
@@ -619,3 +637,174 @@ class Batch:
 
     def autotune(self, sweeps=32):
         return hdmc_batch_autotune(self.b, sweeps)
+
+
+
+# ---- three dimensions: hard spheres ------------------------------------------------
+
+def hdmc3_create(N, L, sigma, d, nselect, seed, precision, xyz=None, stream=None):
+    h = _vp()
+    arg = None
+    if xyz is not None:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+        arg = _p(xyz, _f64p)
+    _check(lib().hdmc3_create(ctypes.byref(h), N, L[0], L[1], L[2], sigma, d, nselect, seed & 0xFFFFFFFFFFFFFFFF,
+                              _precision(precision), arg, stream), "hdmc3_create")
+    return h
+
+
+def hdmc3_sweep(h, n):
+    _check(lib().hdmc3_sweep(h, n), "hdmc3_sweep")
+
+
+def hdmc3_shift(h):
+    _check(lib().hdmc3_shift(h), "hdmc3_shift")
+
+
+def hdmc3_subsweep(h, sweep, Q):
+    _check(lib().hdmc3_subsweep(h, sweep, Q), "hdmc3_subsweep")
+
+
+def hdmc3_sample(h):
+    _check(lib().hdmc3_sample(h), "hdmc3_sample")
+
+
+def hdmc3_pressure(h):
+    """Returns (betaP_over_rho, g_contact, hist[200] uint64, n_samples)."""
+    bp, g0 = ctypes.c_double(), ctypes.c_double()
+    ns = ctypes.c_int64()
+    hist = np.zeros(HDMC_HIST_BINS, dtype=np.uint64)
+    _check(lib().hdmc3_pressure(h, ctypes.byref(bp), ctypes.byref(g0), _p(hist, _u64p), ctypes.byref(ns)),
+           "hdmc3_pressure")
+    return bp.value, g0.value, hist, ns.value
+
+
+def hdmc3_positions(h, N):
+    xyz = np.zeros(3 * N, dtype=np.float64)
+    _check(lib().hdmc3_positions(h, _p(xyz, _f64p)), "hdmc3_positions")
+    return xyz.reshape(N, 3)
+
+
+def hdmc3_get_state(h, C):
+    loc = np.zeros(24 * C, dtype=np.float64)
+    cnt = np.zeros(C, dtype=np.uint8)
+    _check(lib().hdmc3_get_state(h, _p(loc, _f64p), _p(cnt, _u8p)), "hdmc3_get_state")
+    return loc.reshape(C, 8, 3), cnt
+
+
+def hdmc3_counters(h):
+    out = np.zeros(4, dtype=np.uint64)
+    _check(lib().hdmc3_counters(h, _p(out, _u64p)), "hdmc3_counters")
+    return out
+
+
+def hdmc3_info(h):
+    m = np.zeros(3, dtype=np.int32)
+    w = np.zeros(3, dtype=np.float64)
+    org = np.zeros(3, dtype=np.float64)
+    sw, sh = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().hdmc3_info(h, _p(m, _i32p), _p(w, _f64p), _p(org, _f64p), ctypes.byref(sw), ctypes.byref(sh)),
+           "hdmc3_info")
+    return {"m": m, "w": w, "origin": org, "sweeps_done": sw.value, "shifts_done": sh.value}
+
+
+def hdmc3_set_move_size(h, d):
+    _check(lib().hdmc3_set_move_size(h, d), "hdmc3_set_move_size")
+
+
+def hdmc3_set_balance(h, shuffle_particles, shuffle_sets):
+    _check(lib().hdmc3_set_balance(h, int(bool(shuffle_particles)), int(bool(shuffle_sets))), "hdmc3_set_balance")
+
+
+def hdmc3_sync(h):
+    _check(lib().hdmc3_sync(h), "hdmc3_sync")
+
+
+def hdmc3_profile_sweeps(h, n):
+    """Mean ms per (sub-sweep, shift) launch over n sweeps."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hdmc3_profile_sweeps(h, n, ctypes.byref(a), ctypes.byref(b)), "hdmc3_profile_sweeps")
+    return a.value, b.value
+
+
+def hdmc3_destroy(h):
+    if h is not None and h.value:
+        lib().hdmc3_destroy(h)
+
+
+class System3:
+    """One hard-sphere system on the current CUDA device (work goes to torch's
+    current stream unless a stream is given).  xyz: global start positions,
+    else the face-centred cubic start (N = 4 q^3)."""
+
+    def __init__(self, N, L, sigma=1.0, d=0.1, nselect=4, seed=1, precision="fp32", xyz=None, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.N, self.L, self.sigma = N, tuple(float(x) for x in L), sigma
+        self.precision = _precision(precision)
+        self.h = None
+        self.h = hdmc3_create(N, self.L, sigma, d, nselect, seed, self.precision, xyz, stream)
+        info = hdmc3_info(self.h)
+        self.m, self.w = info["m"], info["w"]
+        self.C = int(np.prod(self.m.astype(np.int64)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            hdmc3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        hdmc3_sweep(self.h, n)
+
+    def shift(self):
+        hdmc3_shift(self.h)
+
+    def subsweep(self, sweep, Q):
+        hdmc3_subsweep(self.h, sweep, Q)
+
+    def sample(self):
+        hdmc3_sample(self.h)
+
+    def pressure(self):
+        return hdmc3_pressure(self.h)
+
+    def positions(self):
+        return hdmc3_positions(self.h, self.N)
+
+    def state(self):
+        return hdmc3_get_state(self.h, self.C)
+
+    def counters(self):
+        return hdmc3_counters(self.h)
+
+    def info(self):
+        return hdmc3_info(self.h)
+
+    def origin(self):
+        return hdmc3_info(self.h)["origin"]
+
+    def set_move_size(self, d):
+        hdmc3_set_move_size(self.h, d)
+
+    def set_balance(self, shuffle_particles=True, shuffle_sets=True):
+        hdmc3_set_balance(self.h, shuffle_particles, shuffle_sets)
+
+    def sync(self):
+        hdmc3_sync(self.h)
+
+    def profile_sweeps(self, n):
+        return hdmc3_profile_sweeps(self.h, n)
+
+    def box(self):
+        """Periodic box of the precision's geometry (binary32 cell widths in fp32)."""
+        if self.precision == HDMC_FP64:
+            return np.array(self.L)
+        return self.m * self.w.astype(np.float32).astype(np.float64)

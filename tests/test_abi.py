@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     txt = open(os.path.join(ROOT, "include", "hdmc.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(hdmc_\w+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(hdmc3?_\w+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -24,7 +24,8 @@ def libpath():
 
 def test_header_declares_entry_points():
     names = _declared()
-    for n in ["hdmc_create", "hdmc_sweep", "hdmc_shift", "hdmc_pressure", "hdmc_positions", "hdmc_destroy"]:
+    for n in ["hdmc_create", "hdmc_sweep", "hdmc_shift", "hdmc_pressure", "hdmc_positions", "hdmc_destroy",
+              "hdmc3_create", "hdmc3_sweep", "hdmc3_shift", "hdmc3_pressure", "hdmc3_positions", "hdmc3_destroy"]:
         assert n in names
 
 
