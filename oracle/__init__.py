@@ -101,7 +101,7 @@ def lib():
             "orc3_set_balance": (None, [vp, ctypes.c_int, ctypes.c_int]),
             "orc3_sweep_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, _f64p, _i32p, _i32p, _f64p]),
             "orc3_cell_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _f64p]),
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _f64p]),
             "orc3_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
             "orc3_shift": (ctypes.c_int, [vp]),
             "orc3_subsweep": (None, [vp, ctypes.c_uint32, ctypes.c_int]),
@@ -408,11 +408,12 @@ def sweep_draws3(seed, sweep, w):
     return perm, f.value, ds.value
 
 
-def cell_draws3(seed, sweep, cell, Q, n, nsel, shuffle=True):
+def cell_draws3(seed, sweep, cell, Q, n, nsel, shuffle=True, precision=FP64):
     """(perm[:n], uvw[nsel, 3]) of one 3-d cell update."""
     perm = np.zeros(8, dtype=np.int32)
     uvw = np.zeros(3 * nsel, dtype=np.float64)
-    lib().orc3_cell_draws(seed, sweep, cell, Q, n, int(shuffle), nsel, _p(perm, _i32p), _p(uvw, _f64p))
+    lib().orc3_cell_draws(seed, sweep, cell, Q, n, int(shuffle), nsel, precision, _p(perm, _i32p),
+                          _p(uvw, _f64p))
     return perm[:n], uvw.reshape(nsel, 3)
 
 

@@ -1236,9 +1236,10 @@ int orc_local_overlaps(const oracle_t *o) { return (int)count_overlaps_local(o);
 /*  - trial displacement uniform in a ball of radius d (the "maximum move    */
 /*    radius" of Sec. 3.3), by rejection from (-1,1)^3;                     */
 /*  - the shift direction is one of +-x, +-y, +-z (Alg. 4 with three axes); */
-/*  - binary32 mode: the same binary64 draws, rounded to binary32 for the   */
-/*    move; positions, widths and pair tests in binary32 as in two          */
-/*    dimensions (trial position and overlap predicate by fma).             */
+/*  - binary32 mode: directions from 21-bit fields as in two dimensions   */
+/*    (three fields per attempt, two attempts per Philox block); positions, */
+/*    widths and pair tests in binary32 (trial position and overlap         */
+/*    predicate by fma).                                                    */
 /* ======================================================================== */
 #define NMAX3 8
 
@@ -1539,11 +1540,17 @@ void orc3_sweep_draws(uint64_t seed, uint32_t sweep, const double w[3], int32_t 
 
 /* Draws of one cell update (sweep s, set Q, canonical cell c): shuffle
  * stream S = (s, c, (0<<28)|(Q<<24)) gives k = bounded(n!) when n >= 2 and
- * the particle shuffle is on; trial stream T = (s, c, (1<<28)|(Q<<24)) is
- * read as consecutive words, six per attempt: u = sym52(w0,w1),
- * v = sym52(w2,w3), s = sym52(w4,w5), kept when (u*u + v*v) + s*s < 1. */
+ * the particle shuffle is on (both modes); trial stream
+ * T = (s, c, (1<<28)|(Q<<24)) gives the directions, uniform in the unit ball
+ * by rejection from (-1,1)^3:
+ *   binary64: consecutive words, six per attempt: u = sym52(w0,w1),
+ *             v = sym52(w2,w3), s = sym52(w4,w5), kept when
+ *             (u*u + v*v) + s*s < 1;
+ *   binary32: block b cut into six 21-bit fields; attempts are the field
+ *             triples (0,1,2), (3,4,5) of blocks 0, 1, ...: u = sym21,
+ *             kept when fma(u, u, fma(v, v, s*s)) < 1 in binary32. */
 static void cell_draws3(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
-                        int perm[8], double *U)
+                        int prec, int perm[8], double *U)
 {
     const uint32_t setbits = (uint32_t)Q << 24;
     for (int j = 0; j < 8; ++j) perm[j] = j;
@@ -1552,27 +1559,45 @@ static void cell_draws3(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int
         stream_open(&s, seed, sweep, cell, (DOM_SHUFFLE << 28) | setbits);
         decode_perm8(n, stream_bounded(&s, kFactorial8[n]), perm);
     }
-    stream_t t;
-    stream_open(&t, seed, sweep, cell, (DOM_TRIAL << 28) | setbits);
-    for (int k = 0; k < nsel;) {
-        double u[3];
-        for (int a = 0; a < 3; ++a) {
-            uint32_t hi = stream_word(&t), lo = stream_word(&t);
-            u[a] = sym52(hi, lo);
+    if (prec == 0) {
+        stream_t t;
+        stream_open(&t, seed, sweep, cell, (DOM_TRIAL << 28) | setbits);
+        for (int k = 0; k < nsel;) {
+            double u[3];
+            for (int a = 0; a < 3; ++a) {
+                uint32_t hi = stream_word(&t), lo = stream_word(&t);
+                u[a] = sym52(hi, lo);
+            }
+            if ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] < 1.0) {
+                U[3 * k] = u[0]; U[3 * k + 1] = u[1]; U[3 * k + 2] = u[2];
+                ++k;
+            }
         }
-        if ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] < 1.0) {
-            U[3 * k] = u[0]; U[3 * k + 1] = u[1]; U[3 * k + 2] = u[2];
-            ++k;
+    } else {
+        uint32_t block = 0, w[4], f[6];
+        int triple = 2;
+        for (int k = 0; k < nsel;) {
+            if (triple == 2) {
+                philox_block(seed, sweep, cell, (DOM_TRIAL << 28) | setbits, block++, w);
+                fields21(w, f);
+                triple = 0;
+            }
+            float u = sym21(f[3 * triple]), v = sym21(f[3 * triple + 1]), t = sym21(f[3 * triple + 2]);
+            ++triple;
+            if (fmaf(u, u, fmaf(v, v, t * t)) < 1.0f) {
+                U[3 * k] = u; U[3 * k + 1] = v; U[3 * k + 2] = t;
+                ++k;
+            }
         }
     }
 }
 
 /* Test hook: the draws of one cell update (perm[8], uvw[3*nsel]). */
-void orc3_cell_draws(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel,
+void orc3_cell_draws(uint64_t seed, uint32_t sweep, uint32_t cell, int Q, int n, int shuffle, int nsel, int prec,
                      int32_t perm[8], double *uvw)
 {
     int p[8];
-    cell_draws3(seed, sweep, cell, Q, n, shuffle, nsel, p, uvw);
+    cell_draws3(seed, sweep, cell, Q, n, shuffle, nsel, prec, p, uvw);
     for (int j = 0; j < 8; ++j) perm[j] = p[j];
 }
 
@@ -1584,7 +1609,7 @@ static void cell_update3(oracle3_t *o, uint32_t sweep, int Q, int cx, int cy, in
     if (n == 0) return;
     int perm[8];
     double U[3 * 256];
-    cell_draws3(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, perm, U);
+    cell_draws3(o->seed, sweep, (uint32_t)c, Q, n, o->shuffle_particles, o->nsel, o->prec, perm, U);
     const int cc[3] = {cx, cy, cz};
     if (o->prec == 0) {
         double *X = o->P + 3 * NMAX3 * c;
@@ -1640,7 +1665,7 @@ static void cell_update3(oracle3_t *o, uint32_t sweep, int Q, int cx, int cy, in
             float p[3];
             int inside = 1;
             for (int a = 0; a < 3; ++a) {
-                p[a] = fmaf(df, (float)U[3 * t + a], X[3 * i + a]);
+                p[a] = fmaf(df, (float)U[3 * t + a], X[3 * i + a]);   /* U exact in binary32 */
                 if (!(p[a] >= 0.0f && p[a] < o->wf[a])) inside = 0;
             }
             acc[0]++;

@@ -17,9 +17,11 @@
 //                                    distance unif53 * w/2
 //   explicit shift k:                (k, 0xFFFFFFFF, 4<<28): f, distance
 //   shuffle of cell c, sweep s, Q:   (s, c, (0<<28)|(Q<<24)): k in [0, n!)
-//   trials of that update:           (s, c, (1<<28)|(Q<<24)): consecutive
-//                                    words, six per attempt (three sym52),
-//                                    kept inside the unit ball
+//   trials of that update:           (s, c, (1<<28)|(Q<<24)): directions
+//                                    kept inside the unit ball (binary64:
+//                                    six words per attempt, three sym52;
+//                                    binary32: two attempts of three 21-bit
+//                                    fields per block)
 //   start jitter of sphere p:        (p, 0xFFFFFFFE, 3<<28)
 //
 // Sub-sweep kernel: one thread per active cell.  Before its trials a thread
@@ -33,6 +35,7 @@
 #include <vector>
 
 #include "hdmc.h"
+#include "hdmc_common.cuh"
 #include "hdmc_device.cuh"
 
 namespace hdmc {
@@ -215,21 +218,50 @@ __device__ __forceinline__ bool inside_ball(const uint32_t (&w)[6]) {
     return (u0 * u0 + u1 * u1) + u2 * u2 < 1.0;
 }
 
-// binary32 rounding of sym52(hi, lo) = m 2^-52, m = 2k + 1 - 2^52: rounding
-// commutes with the power-of-two scale, so it is the rounded integer m
-// times 2^-52.
-__device__ __forceinline__ float sym52_f32(uint32_t hi, uint32_t lo) {
-    const uint64_t k = (((uint64_t)hi << 32) | lo) >> 12;
-    const long long m = (long long)(2 * k + 1) - (1LL << 52);
-    return __ll2float_rn(m) * 0x1p-52f;
-}
-
-template <typename T> struct Dir3;
-template <> struct Dir3<float> {
-    __device__ static float get(uint32_t hi, uint32_t lo) { return sym52_f32(hi, lo); }
+// Trial directions of one cell update, uniform in the unit ball by
+// rejection from (-1,1)^3.
+//   binary64: consecutive words of the trial stream, six per attempt,
+//             three sym52 variates;
+//   binary32: each Philox block of the trial stream cut into six 21-bit
+//             fields, two attempts of three sym21 variates per block, kept
+//             when fma(u, u, fma(v, v, s*s)) < 1.
+template <typename T> struct TrialDir;
+template <> struct TrialDir<double> {
+    WordStream ws;
+    __device__ TrialDir(const G3& g, uint32_t sweep, uint32_t c, uint32_t dom) : ws(g.key0, g.key1, sweep, c, dom) {}
+    __device__ __forceinline__ void next(double& u0, double& u1, double& u2) {
+        uint32_t wd[6];
+        for (;;) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) wd[q] = ws.next();
+            if (inside_ball(wd)) break;
+        }
+        u0 = sym52(wd[0], wd[1]);
+        u1 = sym52(wd[2], wd[3]);
+        u2 = sym52(wd[4], wd[5]);
+    }
 };
-template <> struct Dir3<double> {
-    __device__ static double get(uint32_t hi, uint32_t lo) { return sym52(hi, lo); }
+template <> struct TrialDir<float> {
+    uint32_t k0, k1, sweep, c, dom, block;
+    uint32_t f[6];
+    int triple;
+    __device__ TrialDir(const G3& g, uint32_t sweep_, uint32_t c_, uint32_t dom_)
+        : k0(g.key0), k1(g.key1), sweep(sweep_), c(c_), dom(dom_), block(0), triple(2) {}
+    __device__ __forceinline__ void next(float& u0, float& u1, float& u2) {
+        for (;;) {
+            if (triple == 2) {
+                fields21(philox4x32_10(make_uint4(sweep, c, dom, block), k0, k1), f);
+                ++block;
+                triple = 0;
+            }
+            const bool second = triple == 1;
+            u0 = sym21(second ? f[3] : f[0]);
+            u1 = sym21(second ? f[4] : f[1]);
+            u2 = sym21(second ? f[5] : f[2]);
+            ++triple;
+            if (fmaf(u0, u0, fmaf(u1, u1, u2 * u2)) < 1.0f) return;
+        }
+    }
 };
 
 // Pair test on binary32 copies of the coordinates: 1 overlap, 0 none, 2 too
@@ -297,20 +329,21 @@ __device__ bool neighbour_hit_global(const G3& g, const T* cells, int cx, int cy
 }
 
 // Gather the occupied slots of one neighbour cell (offset dx,dy,dz, storage
-// index sn) that lie within reach of the active cell [0,w)^3: their binary32
-// image coordinates, and sn, go to the thread's candidate list.
+// index sn) that lie within reach of the box [lo, hi] that holds every trial
+// position of this cell update: their binary32 image coordinates, and sn, go
+// to the thread's candidate list.
 template <typename T>
 __device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const T (&qy)[8], const T (&qz)[8],
-                                            int dx, int dy, int dz, unsigned sn, float4 (*cand)[kSubB3], int& nc) {
-    const float w0 = g.wf[0], w1 = g.wf[1], w2 = g.wf[2];
-    const float sx = (float)dx * w0, sy = (float)dy * w1, sz = (float)dz * w2;
+                                            int dx, int dy, int dz, unsigned sn, const float (&lo)[3],
+                                            const float (&hi)[3], float4 (*cand)[kSubB3], int& nc) {
+    const float sx = (float)dx * g.wf[0], sy = (float)dy * g.wf[1], sz = (float)dz * g.wf[2];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         if (qx[j] != (T)kEmpty) {
             const float ex = (float)qx[j] + sx, ey = (float)qy[j] + sy, ez = (float)qz[j] + sz;
-            const float gx = ex < 0.0f ? -ex : (ex > w0 ? ex - w0 : 0.0f);
-            const float gy = ey < 0.0f ? -ey : (ey > w1 ? ey - w1 : 0.0f);
-            const float gz = ez < 0.0f ? -ez : (ez > w2 ? ez - w2 : 0.0f);
+            const float gx = ex < lo[0] ? lo[0] - ex : (ex > hi[0] ? ex - hi[0] : 0.0f);
+            const float gy = ey < lo[1] ? lo[1] - ey : (ey > hi[1] ? ey - hi[1] : 0.0f);
+            const float gz = ez < lo[2] ? lo[2] - ez : (ez > hi[2] ? ez - hi[2] : 0.0f);
             if (gx * gx + gy * gy + gz * gz < g.keep2f) {
                 if (nc < kCand3) cand[nc][threadIdx.x] = make_float4(ex, ey, ez, __uint_as_float(sn));
                 ++nc;
@@ -350,6 +383,31 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                 WordStream S(g.key0, g.key1, dr.sweep, c, (kDomShuffle << 28) | setbits);
                 shuffle3(x, y, z, n, S.bounded(factorial8(n)));
             }
+            // Every trial position lies in the box [lo, hi]: a sphere makes at
+            // most K = ceil(n_M / n) trials, each moving it by less than d per
+            // axis from where the previous accepted one left it, and positions
+            // outside [0, w) are rejected before any overlap test.
+            float lo[3], hi[3];
+            {
+                const int K = (g.nsel + n - 1) / n;
+                const float reach = (float)K * g.df * (1.0f + 1.0e-5f) + 1.0e-6f;
+                float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < n) {
+                        const float v[3] = {(float)x[j], (float)y[j], (float)z[j]};
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            mn[a] = fminf(mn[a], v[a]);
+                            mx[a] = fmaxf(mx[a], v[a]);
+                        }
+                    }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = fmaxf(0.0f, mn[a] - reach);
+                    hi[a] = fminf(g.wf[a], mx[a] + reach);
+                }
+            }
             int nc = 0;
 #pragma unroll 1
             for (int row = 0; row < 9; ++row) {
@@ -365,7 +423,7 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                     }
 #pragma unroll
                     for (int e = 0; e < 3; ++e)
-                        if (e != 1 || row != 4) gather_cell(g, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], cand, nc);
+                        if (e != 1 || row != 4) gather_cell(g, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], lo, hi, cand, nc);
                 } else {
 #pragma unroll 1
                     for (int e = 0; e < 3; ++e) {
@@ -373,7 +431,7 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                         const unsigned sn = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
                         T ax[8], ay[8], az[8];
                         ld_cell3(cells + (size_t)sn * kCell3, ax, ay, az);
-                        gather_cell(g, ax, ay, az, e - 1, dy, dz, sn, cand, nc);
+                        gather_cell(g, ax, ay, az, e - 1, dy, dz, sn, lo, hi, cand, nc);
                     }
                 }
             }
@@ -386,18 +444,14 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                 fz[j] = (float)z[j];
             }
             const T w0 = A::w(g, 0), w1 = A::w(g, 1), w2 = A::w(g, 2);
-            WordStream TS(g.key0, g.key1, dr.sweep, c, (kDomTrial << 28) | setbits);
+            TrialDir<T> TD(g, dr.sweep, c, (kDomTrial << 28) | setbits);
             int i = 0;
             for (int t = 0; t < g.nsel; ++t) {
-                uint32_t wd[6];
-                for (;;) {
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) wd[q] = TS.next();
-                    if (inside_ball(wd)) break;
-                }
-                const T px = A::trial(g, pick8(x, i), Dir3<T>::get(wd[0], wd[1]));
-                const T py = A::trial(g, pick8(y, i), Dir3<T>::get(wd[2], wd[3]));
-                const T pz = A::trial(g, pick8(z, i), Dir3<T>::get(wd[4], wd[5]));
+                T u0, u1, u2;
+                TD.next(u0, u1, u2);
+                const T px = A::trial(g, pick8(x, i), u0);
+                const T py = A::trial(g, pick8(y, i), u1);
+                const T pz = A::trial(g, pick8(z, i), u2);
                 ++n_tr;
                 if (!(px >= (T)0 && px < w0 && py >= (T)0 && py < w1 && pz >= (T)0 && pz < w2)) {
                     ++n_lf;

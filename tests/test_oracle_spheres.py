@@ -229,8 +229,9 @@ def test_cell_shuffles_uniform():
     assert chi2.pvalue > 1e-4
 
 
-def test_ball_directions_uniform():
-    u = np.vstack([O.cell_draws3(5, 3, c, 2, 1, 8)[1] for c in range(4000)])
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_ball_directions_uniform(prec):
+    u = np.vstack([O.cell_draws3(5, 3, c, 2, 1, 8, precision=prec)[1] for c in range(4000)])
     r = np.linalg.norm(u, axis=1)
     assert r.max() < 1.0
     assert stats.kstest(r**3, "uniform").pvalue > 1e-4
@@ -238,9 +239,29 @@ def test_ball_directions_uniform():
     phi = (np.arctan2(u[:, 1], u[:, 0]) + math.pi) / (2 * math.pi)
     assert stats.kstest(phi, "uniform").pvalue > 1e-4
     # each trial's draws do not depend on the cell's population
-    a = O.cell_draws3(5, 3, 17, 2, 1, 8)[1]
-    b = O.cell_draws3(5, 3, 17, 2, 7, 8)[1]
+    a = O.cell_draws3(5, 3, 17, 2, 1, 8, precision=prec)[1]
+    b = O.cell_draws3(5, 3, 17, 2, 7, 8, precision=prec)[1]
     assert np.array_equal(a, b)
+    # mirror symmetry of the variates: the lattices are symmetric about 0
+    if prec == O.FP32:
+        assert np.all(np.abs(u) * 2**21 % 2 == 1)          # odd multiples of 2^-21
+    else:
+        assert np.all(np.abs(u) * 2**52 % 2 == 1)          # odd multiples of 2^-52
+
+
+def test_binary32_directions_are_the_21bit_field_triples():
+    # attempts come from block b's fields (0,1,2) and (3,4,5) in order; with
+    # rejections the kept ones are a subsequence of the attempts
+    seed, sweep, cell, Q = 9, 4, 33, 6
+    kept = O.cell_draws3(seed, sweep, cell, Q, 1, 12, precision=O.FP32)[1]
+    attempts = []
+    for b in range(40):
+        f = O.fields21(O.philox([sweep, cell, (1 << 28) | (Q << 24), b], [seed & 0xFFFFFFFF, seed >> 32]))
+        for t in range(2):
+            a = np.array([(2 * int(x) + 1 - 2**21) * 2.0**-21 for x in f[3 * t:3 * t + 3]])
+            attempts.append(a)
+    inside = [a for a in attempts if (a**2).sum() < 1 - 1e-6]
+    assert np.array_equal(kept, np.array(inside[:12]))
 
 
 def test_sweep_draws3():
@@ -295,7 +316,8 @@ def test_two_spheres_sample_the_uniform_distribution():
                 assert stats.kstest(slab[:, b] / 2, "uniform").statistic < crit
 
 
-def test_four_spheres_match_rejection_sampling():
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_four_spheres_match_rejection_sampling(prec):
     L = 4.4
     rng = np.random.default_rng(9)
     pairs = [(i, j) for i in range(4) for j in range(i + 1, 4)]
@@ -310,7 +332,7 @@ def test_four_spheres_match_rejection_sampling():
         if dm >= 1.0:
             ref.append(dm)
     start = np.array([[0.5, 0.5, 0.5], [2.7, 0.5, 0.5], [0.5, 2.7, 2.7], [2.7, 2.7, 0.5]])
-    s = O.System3(4, [L] * 3, 1.0, 0.4, 4, 78, O.FP64, xyz=start)
+    s = O.System3(4, [L] * 3, 1.0, 0.4, 4, 78, prec, xyz=start)
     s.sweep(200)
     mc = []
     for _ in range(12000):
