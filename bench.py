@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 SWEEPS_PER_STEP = 100
 METRIC = "trial moves/sec at N=1M phi=0.716 (1 GB300), FP32-local vs FP64; % HBM roofline"
 KERNELS_PER_SWEEP = 5          # 4 sub-sweeps + 1 cell shift
+SPHERE_KERNELS_PER_SWEEP = 9   # 8 sub-sweeps + 1 cell shift (three dimensions)
 GRAPH_CHUNK = 64               # sweeps per recorded graph (one draws kernel each)
 
 
@@ -47,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-replica batch leg")
     ap.add_argument("--no-n4m", action="store_true", help="skip the N=4M legs")
-    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m"],
+    ap.add_argument("--no-spheres", action="store_true", help="skip the hard-sphere (3-d) legs")
+    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
@@ -59,6 +61,15 @@ def ncu_case(args):
     import torch
     from paper_1211_1646_gb300 import build, hdmc, workloads
     build.build()
+    if args.ncu_case == "spheres":
+        w = workloads.spheres_n1m_phi049(args.precision)
+        s = hdmc.System3(w.N, w.L, 1.0, w.d, w.nselect, 1, args.precision)
+        s.sweep(3)
+        s.sample()
+        s.pressure()
+        torch.cuda.synchronize()
+        print("ncu case %s %s done: counters %s" % (w.name, args.precision, list(s.counters())))
+        return
     w = workloads.n1m_phi0716() if args.ncu_case == "n1m" else workloads.n4m(0.716)
     s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, args.precision)
     s.sweep(3)
@@ -76,23 +87,26 @@ def workload():
 SUBSWEEP_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc_subsweep.cuh")
 
 
-def subsweep_source_hash():
-    """First 16 hex digits of the SHA-256 of the sub-sweep kernel's sources."""
+SPHERE_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc3.cu")
+
+
+def subsweep_source_hash(sources=SUBSWEEP_SOURCES):
+    """First 16 hex digits of the SHA-256 of a kernel's sources."""
     import hashlib
     h = hashlib.sha256()
-    for name in SUBSWEEP_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_1211_1646_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary="subsweep_f32_n1m.md"):
+def profiled_traffic(summary="subsweep_f32_n1m.md", sources=SUBSWEEP_SOURCES):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
     summary, or None when the kernel's sources changed since the capture."""
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        src_hash = subsweep_source_hash()
+        src_hash = subsweep_source_hash(sources)
     except OSError:
         return None
     t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
@@ -100,6 +114,10 @@ def profiled_traffic(summary="subsweep_f32_n1m.md"):
     if not t or not h or h.group(1) != src_hash:
         return None
     return int(t.group(1))
+
+
+def profiled_traffic_spheres():
+    return profiled_traffic("subsweep3_f32_n1m.md", SPHERE_SOURCES)
 
 
 # ALU work of one binary32 trial move (Alg. 2), in 32-bit lane operations
@@ -377,6 +395,38 @@ def run_hdmc(args, rank, world, dist):
                              "d = 0.08, autotuned (16 sweeps per candidate)"}
         b.close()
 
+    # ---- hard spheres (three dimensions): N = 4*64^3 at phi = 0.49 ----
+    spheres = None
+    if not args.no_spheres:
+        w3 = workloads.spheres_n1m_phi049("fp32")
+        spheres = {"workload": w3.name, "N": w3.N, "phi": w3.phi, "box": [round(x, 4) for x in w3.L],
+                   "d": w3.d, "nselect": w3.nselect, "unit": "trial moves/s",
+                   "step": "%d sweeps (8 sub-sweeps + 1 shift each) + contact histogram + pressure fit"
+                           % SWEEPS_PER_STEP,
+                   "launches_per_step": SPHERE_KERNELS_PER_SWEEP * SWEEPS_PER_STEP
+                                        + math.ceil(SWEEPS_PER_STEP / GRAPH_CHUNK) + 1}
+        for prec, nsteps in (("fp32", args.steps), ("fp64", max(1, args.fp64_steps - 1))):
+            s3 = hdmc.System3(w3.N, w3.L, 1.0, w3.d, w3.nselect, seed, prec)
+            t3, ms3, p3 = timed_steps(s3, nsteps, 1)
+            ms3 = max_over_ranks(ms3)
+            sub3, shift3 = s3.profile_sweeps(8)
+            cell_bytes = 24 * (4 if prec == "fp32" else 8)
+            # algorithmic bytes of one sub-sweep launch: every cell read once
+            # (the neighbourhoods of the active cells cover the grid) and the
+            # active set (one eighth of the cells) written once
+            bytes3 = (s3.C + s3.C // 8) * cell_bytes
+            ach = bytes3 / (sub3 / 1e3) / 1e9
+            leg = {"value": sum_over_ranks(t3) / (ms3 / 1e3), "ms_per_step": ms3 / nsteps, "steps": nsteps,
+                   "subsweep_ms": sub3, "shift_ms": shift3, "betaP_over_rho_last": p3[-1] if p3 else None}
+            if prec == "fp32":
+                leg["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": ach / hbm_peak, "traffic": profiled_traffic_spheres(),
+                                   "kernel": "k_sub3<float>", "peak_kind": peak_kind,
+                                   "ms_per_launch": sub3, "algorithmic_bytes_per_launch": bytes3}
+            spheres[prec] = leg
+            s3.close()
+        spheres["value"] = spheres["fp32"]["value"]
+
     launches_per_step = KERNELS_PER_SWEEP * SWEEPS_PER_STEP + math.ceil(SWEEPS_PER_STEP / GRAPH_CHUNK) + 1
     line = {
         "metric": METRIC,
@@ -416,6 +466,7 @@ def run_hdmc(args, rank, world, dist):
         "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
         "batch64": batch,
         "n4m": n4m,
+        "spheres": spheres,
         "pressure_betaP_over_rho_last": press[-1] if press else None,
     }
     return line

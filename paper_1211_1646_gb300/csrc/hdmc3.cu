@@ -49,7 +49,7 @@ void squared_edges(double sigma, double* E);
 constexpr int kSlots3 = 8;          // sum of w^2 < 4 sigma^2 => at most 8 centres per cell
 constexpr int kCell3 = 3 * kSlots3;  // coordinates per cell
 constexpr int kSubB3 = 64;          // sub-sweep block: 64 active cells
-constexpr int kCand3 = 28;          // gathered neighbour spheres per cell (more: read from global)
+constexpr int kCand3 = 24;          // gathered neighbour spheres per cell (more: read from global)
 constexpr int kShiftB3 = 256;
 constexpr int kHistB3 = 128;
 constexpr int kDrawChunk3 = 64;     // sweeps per draws launch
@@ -341,10 +341,10 @@ __device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const
     for (int j = 0; j < 8; ++j) {
         if (qx[j] != (T)kEmpty) {
             const float ex = (float)qx[j] + sx, ey = (float)qy[j] + sy, ez = (float)qz[j] + sz;
-            const float gx = ex < lo[0] ? lo[0] - ex : (ex > hi[0] ? ex - hi[0] : 0.0f);
-            const float gy = ey < lo[1] ? lo[1] - ey : (ey > hi[1] ? ey - hi[1] : 0.0f);
-            const float gz = ez < lo[2] ? lo[2] - ez : (ez > hi[2] ? ez - hi[2] : 0.0f);
-            if (gx * gx + gy * gy + gz * gz < g.keep2f) {
+            const float gx = fmaxf(fmaxf(lo[0] - ex, ex - hi[0]), 0.0f);
+            const float gy = fmaxf(fmaxf(lo[1] - ey, ey - hi[1]), 0.0f);
+            const float gz = fmaxf(fmaxf(lo[2] - ez, ez - hi[2]), 0.0f);
+            if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < g.keep2f) {
                 if (nc < kCand3) cand[nc][threadIdx.x] = make_float4(ex, ey, ez, __uint_as_float(sn));
                 ++nc;
             }
