@@ -6,9 +6,13 @@
 //
 // Device layout: the cells of one set are contiguous (set-major), row-major
 // over the half-resolution grid within a set, as in two dimensions.  A cell
-// holds 8 slots x 3 coordinates as x0..x7, y0..y7, z0..z7 (96 bytes in
-// binary32, 192 in binary64); slots are filled from slot 0, an unused slot
-// reads kEmpty.
+// has 8 slots, filled from slot 0 (an unused slot reads kEmpty), split in two
+// halves of 4 slots stored as x0..x3, y0..y3, z0..z3 (48 bytes in binary32,
+// 96 in binary64): the primary halves of all C cells, then the secondary
+// halves.  A cell holds 1.2 spheres on average at the densities of interest
+// and more than 4 in about 0.1 % of the cells, so the kernels read a
+// secondary half only when slot 3 is occupied; a secondary half is valid only
+// then, and is written only when the cell holds 4 or more.
 //
 // Random streams (Philox4x32-10 keyed by the seed), with c the canonical cell
 // number (cz*my + cy)*mx + cx:
@@ -48,6 +52,7 @@ void squared_edges(double sigma, double* E);
 
 constexpr int kSlots3 = 8;          // sum of w^2 < 4 sigma^2 => at most 8 centres per cell
 constexpr int kCell3 = 3 * kSlots3;  // coordinates per cell
+constexpr int kHalf3 = 12;           // coordinates per half cell (4 slots)
 constexpr int kSubB3 = 64;          // sub-sweep block: 64 active cells
 constexpr int kCand3 = 24;          // gathered neighbour spheres per cell (more: read from global)
 constexpr int kShiftB3 = 256;
@@ -164,42 +169,82 @@ __device__ __forceinline__ void shuffle3(T (&x)[8], T (&y)[8], T (&z)[8], int n,
 
 __device__ __forceinline__ int wrap3(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
 
-// 256-bit loads and stores of one coordinate part (8 slots) of a cell.
-__device__ __forceinline__ void ld_part(const float* p, float (&v)[8]) {
-    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
-                 : "l"(p));
+// Half-cell loads and stores: 4 slots of one coordinate are 16 bytes
+// (binary32, one 128-bit access) or 32 bytes (binary64, two).
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
-__device__ __forceinline__ void ld_part(const double* p, double (&v)[8]) {
-    const double2* q = reinterpret_cast<const double2*>(p);
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// The 4 slots of one half cell (at p) into slots OFF..OFF+3.
+template <int OFF, typename T>
+__device__ __forceinline__ void ld_half3(const T* p, T (&x)[8], T (&y)[8], T (&z)[8]) {
+    T a[4], b[4], c[4];
+    ld4(p, a);
+    ld4(p + 4, b);
+    ld4(p + 8, c);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const double2 a = q[i];
-        v[2 * i] = a.x;
-        v[2 * i + 1] = a.y;
+        x[OFF + i] = a[i];
+        y[OFF + i] = b[i];
+        z[OFF + i] = c[i];
     }
 }
-__device__ __forceinline__ void st_part(float* p, const float (&v)[8]) {
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
-                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-                 : "memory");
-}
-__device__ __forceinline__ void st_part(double* p, const double (&v)[8]) {
-    double2* q = reinterpret_cast<double2*>(p);
+
+__device__ __forceinline__ size_t primary3(unsigned s) { return (size_t)s * kHalf3; }
+__device__ __forceinline__ size_t secondary3(const G3& g, unsigned s) { return ((size_t)g.C + s) * kHalf3; }
+
+// Completes a cell whose primary half is in slots 0..3: reads the secondary
+// half when slot 3 is occupied, else marks slots 4..7 empty.
+template <typename T>
+__device__ __forceinline__ void ld_rest3(const T* cells, const G3& g, unsigned s, T (&x)[8], T (&y)[8], T (&z)[8]) {
+    if (x[3] != (T)kEmpty) {
+        ld_half3<4>(cells + secondary3(g, s), x, y, z);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+        for (int i = 4; i < 8; ++i) x[i] = y[i] = z[i] = (T)kEmpty;
+    }
 }
+
 template <typename T>
-__device__ __forceinline__ void ld_cell3(const T* p, T (&x)[8], T (&y)[8], T (&z)[8]) {
-    ld_part(p, x);
-    ld_part(p + 8, y);
-    ld_part(p + 16, z);
+__device__ __forceinline__ void ld_cell3(const T* cells, const G3& g, unsigned s, T (&x)[8], T (&y)[8], T (&z)[8]) {
+    ld_half3<0>(cells + primary3(s), x, y, z);
+    ld_rest3(cells, g, s, x, y, z);
 }
+
+// Writes the primary half, and the secondary half when `full` (4 or more
+// spheres: readers then take slot 3 as occupied and read it).
 template <typename T>
-__device__ __forceinline__ void st_cell3(T* p, const T (&x)[8], const T (&y)[8], const T (&z)[8]) {
-    st_part(p, x);
-    st_part(p + 8, y);
-    st_part(p + 16, z);
+__device__ __forceinline__ void st_cell3(T* cells, const G3& g, unsigned s, const T (&x)[8], const T (&y)[8],
+                                         const T (&z)[8], bool full) {
+    T* p = cells + primary3(s);
+    st4(p, x);
+    st4(p + 4, y);
+    st4(p + 8, z);
+    if (full) {
+        T* q = cells + secondary3(g, s);
+        st4(q, x + 4);
+        st4(q + 4, y + 4);
+        st4(q + 8, z + 4);
+    }
+}
+
+// Slot j of cell s (coordinate a at offset 4a); slots 4..7 may be read only
+// when slot 3 is occupied.
+template <typename T>
+__device__ __forceinline__ const T* slot3(const T* cells, const G3& g, unsigned s, int j) {
+    return j < 4 ? cells + primary3(s) + j : cells + secondary3(g, s) + (j - 4);
 }
 
 // Is (hi:lo, ...) an attempt inside the unit ball?  The definition is the
@@ -294,13 +339,12 @@ __device__ bool cell_hit_exact(const G3& g, const T* cells, unsigned sn, int cx,
     int dd[3] = {2 * ix + (int)(Q & 1) - cx, 2 * iy + (int)((Q >> 1) & 1) - cy, 2 * iz + (int)(Q >> 2) - cz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) dd[a] = dd[a] > 1 ? dd[a] - g.m[a] : (dd[a] < -1 ? dd[a] + g.m[a] : dd[a]);
-    const T* nb = cells + (size_t)sn * kCell3;
     const T sx = (T)dd[0] * A::w(g, 0), sy = (T)dd[1] * A::w(g, 1), sz = (T)dd[2] * A::w(g, 2);
     bool hit = false;
     for (int j = 0; j < kSlots3; ++j) {
-        const T qx = nb[j];
-        if (qx == (T)kEmpty) break;
-        hit |= A::hit(g, px - (qx + sx), py - (nb[8 + j] + sy), pz - (nb[16 + j] + sz));
+        const T* q = slot3(cells, g, sn, j);
+        if (q[0] == (T)kEmpty) break;
+        hit |= A::hit(g, px - (q[0] + sx), py - (q[4] + sy), pz - (q[8] + sz));
     }
     return hit;
 }
@@ -315,18 +359,40 @@ __device__ bool neighbour_hit_global(const G3& g, const T* cells, int cx, int cy
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
                 if (dx == 0 && dy == 0 && dz == 0) continue;
-                const T* nb = cells + (size_t)sidx3(g, wrap3(cx + dx, g.m[0]), wrap3(cy + dy, g.m[1]),
-                                                    wrap3(cz + dz, g.m[2])) * kCell3;
+                const unsigned sn = sidx3(g, wrap3(cx + dx, g.m[0]), wrap3(cy + dy, g.m[1]), wrap3(cz + dz, g.m[2]));
                 const T sx = (T)dx * A::w(g, 0), sy = (T)dy * A::w(g, 1), sz = (T)dz * A::w(g, 2);
                 for (int j = 0; j < kSlots3; ++j) {
-                    const T qx = nb[j];
-                    if (qx == (T)kEmpty) break;
-                    const T ex = qx + sx, ey = nb[8 + j] + sy, ez = nb[16 + j] + sz;
+                    const T* q = slot3(cells, g, sn, j);
+                    if (q[0] == (T)kEmpty) break;
+                    const T ex = q[0] + sx, ey = q[4] + sy, ez = q[8] + sz;
                     hit |= A::hit(g, px - ex, py - ey, pz - ez);
                 }
             }
     return hit;
 }
+
+// Per-thread candidate lists in shared memory, column t for thread t:
+// binary32 keeps the three coordinates (12 bytes a candidate); binary64 adds
+// the neighbour cell's storage index for the exact test near contact.
+template <typename T> struct Cand;
+template <> struct Cand<float> {
+    float x[kCand3][kSubB3], y[kCand3][kSubB3], z[kCand3][kSubB3];
+    __device__ __forceinline__ void put(int q, float a, float b, float c, unsigned) {
+        x[q][threadIdx.x] = a;
+        y[q][threadIdx.x] = b;
+        z[q][threadIdx.x] = c;
+    }
+    __device__ __forceinline__ float4 get(int q) const {
+        return make_float4(x[q][threadIdx.x], y[q][threadIdx.x], z[q][threadIdx.x], 0.0f);
+    }
+};
+template <> struct Cand<double> {
+    float4 v[kCand3][kSubB3];
+    __device__ __forceinline__ void put(int q, float a, float b, float c, unsigned sn) {
+        v[q][threadIdx.x] = make_float4(a, b, c, __uint_as_float(sn));
+    }
+    __device__ __forceinline__ float4 get(int q) const { return v[q][threadIdx.x]; }
+};
 
 // Gather the occupied slots of one neighbour cell (offset dx,dy,dz, storage
 // index sn) that lie within reach of the box [lo, hi] that holds every trial
@@ -335,7 +401,7 @@ __device__ bool neighbour_hit_global(const G3& g, const T* cells, int cx, int cy
 template <typename T>
 __device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const T (&qy)[8], const T (&qz)[8],
                                             int dx, int dy, int dz, unsigned sn, const float (&lo)[3],
-                                            const float (&hi)[3], float4 (*cand)[kSubB3], int& nc) {
+                                            const float (&hi)[3], Cand<T>& cand, int& nc) {
     const float sx = (float)dx * g.wf[0], sy = (float)dy * g.wf[1], sz = (float)dz * g.wf[2];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -345,7 +411,7 @@ __device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const
             const float gy = fmaxf(fmaxf(lo[1] - ey, ey - hi[1]), 0.0f);
             const float gz = fmaxf(fmaxf(lo[2] - ez, ez - hi[2]), 0.0f);
             if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < g.keep2f) {
-                if (nc < kCand3) cand[nc][threadIdx.x] = make_float4(ex, ey, ez, __uint_as_float(sn));
+                if (nc < kCand3) cand.put(nc, ex, ey, ez, sn);
                 ++nc;
             }
         }
@@ -359,7 +425,7 @@ template <typename T>
 __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, const Draw3* __restrict__ table,
                                                  int jd, int k, Dev3* st) {
     using A = Ar3<T>;
-    __shared__ float4 cand[kCand3][kSubB3];
+    __shared__ Cand<T> cand;
     const Draw3& dr = table[jd];
     const int Q = dr.perm[k];
     const unsigned s = blockIdx.x * kSubB3 + threadIdx.x;
@@ -370,9 +436,9 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
         const int iy = (int)(r % (unsigned)g.h[1]);
         const int iz = (int)(r / (unsigned)g.h[1]);
         const int cx = 2 * ix + (Q & 1), cy = 2 * iy + ((Q >> 1) & 1), cz = 2 * iz + (Q >> 2);
-        T* own = cells + ((size_t)Q * g.cq + s) * kCell3;
+        const unsigned sown = (unsigned)Q * g.cq + s;
         T x[8], y[8], z[8];
-        ld_cell3(own, x, y, z);
+        ld_cell3(cells, g, sown, x, y, z);
         int n = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) n += x[j] != (T)kEmpty;
@@ -419,8 +485,10 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
                         sn[e] = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
-                        ld_cell3(cells + (size_t)sn[e] * kCell3, ax[e], ay[e], az[e]);
+                        ld_half3<0>(cells + primary3(sn[e]), ax[e], ay[e], az[e]);
                     }
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) ld_rest3(cells, g, sn[e], ax[e], ay[e], az[e]);
 #pragma unroll
                     for (int e = 0; e < 3; ++e)
                         if (e != 1 || row != 4) gather_cell(g, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], lo, hi, cand, nc);
@@ -430,7 +498,7 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                         if (e == 1 && row == 4) continue;
                         const unsigned sn = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
                         T ax[8], ay[8], az[8];
-                        ld_cell3(cells + (size_t)sn * kCell3, ax, ay, az);
+                        ld_cell3(cells, g, sn, ax, ay, az);
                         gather_cell(g, ax, ay, az, e - 1, dy, dz, sn, lo, hi, cand, nc);
                     }
                 }
@@ -467,7 +535,7 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                         }
                     if (!spill) {
                         for (int q = 0; q < nc && !hit; ++q) {
-                            const float4 e = cand[q][threadIdx.x];
+                            const float4 e = cand.get(q);
                             int h = quick_hit<T>(g, pfx - e.x, pfy - e.y, pfz - e.z);
                             if (h == 2) h = cell_hit_exact(g, cells, __float_as_uint(e.w), cx, cy, cz, px, py, pz);
                             hit = h != 0;
@@ -489,7 +557,7 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                 }
                 i = i + 1 == n ? 0 : i + 1;
             }
-            st_cell3(own, x, y, z);
+            st_cell3(cells, g, sown, x, y, z, n > 4);
         }
     }
     const unsigned a = __reduce_add_sync(0xFFFFFFFFu, n_tr), b = __reduce_add_sync(0xFFFFFFFFu, n_ac);
@@ -563,8 +631,8 @@ __global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__
     else if (ax == 1) ny = wrap3(ny + sgn, g.m[1]);
     else nz = wrap3(nz + sgn, g.m[2]);
     T ox[8], oy[8], oz[8], bx[8], by[8], bz[8];
-    ld_cell3(src + (size_t)s * kCell3, ox, oy, oz);
-    ld_cell3(src + (size_t)sidx3(g, nx, ny, nz) * kCell3, bx, by, bz);
+    ld_cell3(src, g, s, ox, oy, oz);
+    ld_cell3(src, g, sidx3(g, nx, ny, nz), bx, by, bz);
     T w, sd, sw, wprev;
     if (sizeof(T) == 8) {
         w = (T)g.w[ax];
@@ -605,7 +673,7 @@ __global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__
         }
     }
     if (k > kSlots3) atomicOr(&st->error, 1u);
-    st_cell3(dst + (size_t)s * kCell3, rx, ry, rz);
+    st_cell3(dst, g, s, rx, ry, rz, k >= 4);
     if (s == 0) st->origin[ax] += (double)sd;
 }
 
@@ -627,14 +695,13 @@ __global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ c
         const unsigned r1 = r0 / (unsigned)g.h[0];
         const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
         const int cx = 2 * ix + (int)(Q & 1), cy = 2 * iy + (int)((Q >> 1) & 1), cz = 2 * iz + (int)(Q >> 2);
-        const T* own = cells + (size_t)s * kCell3;
         double w[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) w[a] = sizeof(T) == 8 ? g.w[a] : (double)g.wf[a];
         for (int i = 0; i < kSlots3; ++i) {
-            const T pxT = own[i];
-            if (pxT == (T)kEmpty) break;
-            const double px = (double)pxT, py = (double)own[8 + i], pz = (double)own[16 + i];
+            const T* own = slot3(cells, g, s, i);
+            if (own[0] == (T)kEmpty) break;
+            const double px = (double)own[0], py = (double)own[4], pz = (double)own[8];
             const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
             for (int dz = -2; dz <= 2; ++dz)
                 for (int dy = -2; dy <= 2; ++dy)
@@ -642,19 +709,19 @@ __global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ c
                         const int nx = ((cx + dx) % g.m[0] + g.m[0]) % g.m[0];
                         const int ny = ((cy + dy) % g.m[1] + g.m[1]) % g.m[1];
                         const int nz = ((cz + dz) % g.m[2] + g.m[2]) % g.m[2];
-                        const T* nb = cells + (size_t)sidx3(g, nx, ny, nz) * kCell3;
+                        const unsigned sn = sidx3(g, nx, ny, nz);
                         const double sx = (double)dx * w[0], sy = (double)dy * w[1], sz = (double)dz * w[2];
                         const float sxf = (float)sx, syf = (float)sy, szf = (float)sz;
                         for (int j = 0; j < kSlots3; ++j) {
-                            const T qxT = nb[j];
-                            if (qxT == (T)kEmpty) break;
+                            const T* q = slot3(cells, g, sn, j);
+                            if (q[0] == (T)kEmpty) break;
                             if (dx == 0 && dy == 0 && dz == 0 && j == i) continue;
-                            const float fx = pxf - ((float)qxT + sxf), fy = pyf - ((float)nb[8 + j] + syf),
-                                        fz = pzf - ((float)nb[16 + j] + szf);
+                            const float fx = pxf - ((float)q[0] + sxf), fy = pyf - ((float)q[4] + syf),
+                                        fz = pzf - ((float)q[8] + szf);
                             const float r2f = fx * fx + fy * fy + fz * fz;
                             if (r2f < lo2f || r2f > hi2f) continue;
-                            const double ex = px - ((double)qxT + sx), ey = py - ((double)nb[8 + j] + sy),
-                                         ez = pz - ((double)nb[16 + j] + sz);
+                            const double ex = px - ((double)q[0] + sx), ey = py - ((double)q[4] + sy),
+                                         ez = pz - ((double)q[8] + sz);
                             const double r2 = (ex * ex + ey * ey) + ez * ez;
                             if (!(r2 >= edges2[0]) || !(r2 < edges2[kHistBins])) continue;
                             int lo = 0, hi = kHistBins;   // largest b with edges2[b] <= r2
@@ -823,6 +890,11 @@ bool any_overlap3(const hdmc3_t* h, const std::vector<double>& loc, const std::v
     return false;
 }
 
+// Element index of slot j, coordinate a of the cell with storage index s.
+size_t host_slot3(const G3& g, size_t s, int j, int a) {
+    return j < 4 ? s * kHalf3 + 4 * a + j : ((size_t)g.C + s) * kHalf3 + 4 * a + (j - 4);
+}
+
 void pack3(const hdmc3_t* h, const std::vector<double>& loc, const std::vector<uint8_t>& cnt, std::vector<char>& raw) {
     const G3& g = h->g;
     raw.assign((size_t)g.C * kCell3 * h->el, 0);
@@ -834,7 +906,7 @@ void pack3(const hdmc3_t* h, const std::vector<double>& loc, const std::vector<u
                 for (int j = 0; j < kSlots3; ++j)
                     for (int a = 0; a < 3; ++a) {
                         const double v = j < cnt[c] ? loc[(8 * c + j) * 3 + a] : kEmpty;
-                        char* dst = raw.data() + (s * kCell3 + 8 * a + j) * h->el;
+                        char* dst = raw.data() + host_slot3(g, s, j, a) * h->el;
                         if (h->prec == HDMC_FP64) std::memcpy(dst, &v, 8);
                         else {
                             const float f = (float)v;
@@ -857,7 +929,7 @@ void unpack3(const hdmc3_t* h, const std::vector<char>& raw, std::vector<double>
                 for (int j = 0; j < kSlots3; ++j) {
                     double v[3];
                     for (int a = 0; a < 3; ++a) {
-                        const char* src = raw.data() + (s * kCell3 + 8 * a + j) * h->el;
+                        const char* src = raw.data() + host_slot3(g, s, j, a) * h->el;
                         if (h->prec == HDMC_FP64) std::memcpy(&v[a], src, 8);
                         else {
                             float f;
@@ -865,7 +937,7 @@ void unpack3(const hdmc3_t* h, const std::vector<char>& raw, std::vector<double>
                             v[a] = f;
                         }
                     }
-                    if (v[0] == kEmpty) continue;
+                    if (v[0] == kEmpty) break;   // slots fill from 0; a secondary half is valid only after a full primary
                     n = j + 1;
                     for (int a = 0; a < 3; ++a) loc[(8 * c + j) * 3 + a] = v[a];
                 }
