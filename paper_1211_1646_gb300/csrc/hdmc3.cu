@@ -394,17 +394,17 @@ template <> struct Cand<double> {
     __device__ __forceinline__ float4 get(int q) const { return v[q][threadIdx.x]; }
 };
 
-// Gather the occupied slots of one neighbour cell (offset dx,dy,dz, storage
-// index sn) that lie within reach of the box [lo, hi] that holds every trial
-// position of this cell update: their binary32 image coordinates, and sn, go
-// to the thread's candidate list.
+// Gather the occupied slots of one half of a neighbour cell (offset
+// dx,dy,dz, storage index sn) that lie within reach of the box [lo, hi] that
+// holds every trial position of this cell update: their binary32 image
+// coordinates (and sn in binary64) go to the thread's candidate list.
 template <typename T>
-__device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const T (&qy)[8], const T (&qz)[8],
+__device__ __forceinline__ void gather_half(const G3& g, const T (&qx)[4], const T (&qy)[4], const T (&qz)[4],
                                             int dx, int dy, int dz, unsigned sn, const float (&lo)[3],
                                             const float (&hi)[3], Cand<T>& cand, int& nc) {
     const float sx = (float)dx * g.wf[0], sy = (float)dy * g.wf[1], sz = (float)dz * g.wf[2];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
         if (qx[j] != (T)kEmpty) {
             const float ex = (float)qx[j] + sx, ey = (float)qy[j] + sy, ez = (float)qz[j] + sz;
             const float gx = fmaxf(fmaxf(lo[0] - ex, ex - hi[0]), 0.0f);
@@ -415,6 +415,22 @@ __device__ __forceinline__ void gather_cell(const G3& g, const T (&qx)[8], const
                 ++nc;
             }
         }
+    }
+}
+
+// Both halves of a neighbour cell whose primary half is already loaded.
+template <typename T>
+__device__ __forceinline__ void gather_cell(const G3& g, const T* cells, const T (&qx)[4], const T (&qy)[4],
+                                            const T (&qz)[4], int dx, int dy, int dz, unsigned sn,
+                                            const float (&lo)[3], const float (&hi)[3], Cand<T>& cand, int& nc) {
+    gather_half(g, qx, qy, qz, dx, dy, dz, sn, lo, hi, cand, nc);
+    if (qx[3] != (T)kEmpty) {
+        const T* p = cells + secondary3(g, sn);
+        T rx[4], ry[4], rz[4];
+        ld4(p, rx);
+        ld4(p + 4, ry);
+        ld4(p + 8, rz);
+        gather_half(g, rx, ry, rz, dx, dy, dz, sn, lo, hi, cand, nc);
     }
 }
 
@@ -480,26 +496,31 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                 const int dz = row / 3 - 1, dy = row % 3 - 1;
                 const int ny = wrap3(cy + dy, g.m[1]), nz = wrap3(cz + dz, g.m[2]);
                 if (sizeof(T) == 4) {
-                    T ax[3][8], ay[3][8], az[3][8];
+                    T ax[3][4], ay[3][4], az[3][4];
                     unsigned sn[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
                         sn[e] = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
-                        ld_half3<0>(cells + primary3(sn[e]), ax[e], ay[e], az[e]);
+                        const T* p = cells + primary3(sn[e]);
+                        ld4(p, ax[e]);
+                        ld4(p + 4, ay[e]);
+                        ld4(p + 8, az[e]);
                     }
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) ld_rest3(cells, g, sn[e], ax[e], ay[e], az[e]);
-#pragma unroll
                     for (int e = 0; e < 3; ++e)
-                        if (e != 1 || row != 4) gather_cell(g, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], lo, hi, cand, nc);
+                        if (e != 1 || row != 4)
+                            gather_cell(g, cells, ax[e], ay[e], az[e], e - 1, dy, dz, sn[e], lo, hi, cand, nc);
                 } else {
 #pragma unroll 1
                     for (int e = 0; e < 3; ++e) {
                         if (e == 1 && row == 4) continue;
                         const unsigned sn = sidx3(g, wrap3(cx + e - 1, g.m[0]), ny, nz);
-                        T ax[8], ay[8], az[8];
-                        ld_cell3(cells, g, sn, ax, ay, az);
-                        gather_cell(g, ax, ay, az, e - 1, dy, dz, sn, lo, hi, cand, nc);
+                        const T* p = cells + primary3(sn);
+                        T ax[4], ay[4], az[4];
+                        ld4(p, ax);
+                        ld4(p + 4, ay);
+                        ld4(p + 8, az);
+                        gather_cell(g, cells, ax, ay, az, e - 1, dy, dz, sn, lo, hi, cand, nc);
                     }
                 }
             }
@@ -534,7 +555,16 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
                             hit |= h != 0;
                         }
                     if (!spill) {
-                        for (int q = 0; q < nc && !hit; ++q) {
+                        int q = 0;
+                        for (; q + 1 < nc && !hit; q += 2) {
+                            const float4 e0 = cand.get(q), e1 = cand.get(q + 1);
+                            int h0 = quick_hit<T>(g, pfx - e0.x, pfy - e0.y, pfz - e0.z);
+                            int h1 = quick_hit<T>(g, pfx - e1.x, pfy - e1.y, pfz - e1.z);
+                            if (h0 == 2) h0 = cell_hit_exact(g, cells, __float_as_uint(e0.w), cx, cy, cz, px, py, pz);
+                            if (h1 == 2) h1 = cell_hit_exact(g, cells, __float_as_uint(e1.w), cx, cy, cz, px, py, pz);
+                            hit = (h0 | h1) != 0;
+                        }
+                        if (q < nc && !hit) {
                             const float4 e = cand.get(q);
                             int h = quick_hit<T>(g, pfx - e.x, pfy - e.y, pfz - e.z);
                             if (h == 2) h = cell_hit_exact(g, cells, __float_as_uint(e.w), cx, cy, cz, px, py, pz);
