@@ -410,11 +410,11 @@ def run_hdmc(args, rank, world, dist):
             t3, ms3, p3 = timed_steps(s3, nsteps, 1)
             ms3 = max_over_ranks(ms3)
             sub3, shift3 = s3.profile_sweeps(8)
-            cell_bytes = 24 * (4 if prec == "fp32" else 8)
-            # algorithmic bytes of one sub-sweep launch: every cell read once
-            # (the neighbourhoods of the active cells cover the grid) and the
-            # active set (one eighth of the cells) written once
-            bytes3 = (s3.C + s3.C // 8) * cell_bytes
+            # algorithmic bytes of one sub-sweep launch, live data only: every
+            # sphere read once (the neighbourhoods of the active cells cover
+            # the grid) and the active set's spheres (one eighth) written
+            # once, 3 coordinates of 4 B (binary32) or 8 B (binary64) each
+            bytes3 = 1.125 * w3.N * 3 * (4 if prec == "fp32" else 8)
             ach = bytes3 / (sub3 / 1e3) / 1e9
             leg = {"value": sum_over_ranks(t3) / (ms3 / 1e3), "ms_per_step": ms3 / nsteps, "steps": nsteps,
                    "subsweep_ms": sub3, "shift_ms": shift3, "betaP_over_rho_last": p3[-1] if p3 else None}

@@ -710,7 +710,20 @@ __global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__
 // Contact histogram: every sphere against the spheres of its 5x5x5 cell
 // neighbourhood; a binary32 estimate of r^2 with a wide margin skips pairs
 // far outside [sigma^2, (sigma + 200 dr)^2), the rest are decided in binary64
-// on r^2 = (dx*dx + dy*dy) + dz*dz against the squared bin edges.
+// on r^2 = (dx*dx + dy*dy) + dz*dz against the squared bin edges.  One thread
+// per cell: its spheres stay in registers while the 125 neighbour cells are
+// read once each.
+__device__ __forceinline__ void hist_bin(double r2, const double* __restrict__ edges2, unsigned int* sh) {
+    if (!(r2 >= edges2[0]) || !(r2 < edges2[kHistBins])) return;
+    int lo = 0, hi = kHistBins;   // largest b with edges2[b] <= r2
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (r2 >= edges2[mid]) lo = mid;
+        else hi = mid;
+    }
+    atomicAdd(&sh[lo], 1u);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ cells,
                                                    const double* __restrict__ edges2, float lo2f, float hi2f,
@@ -725,44 +738,41 @@ __global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ c
         const unsigned r1 = r0 / (unsigned)g.h[0];
         const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
         const int cx = 2 * ix + (int)(Q & 1), cy = 2 * iy + (int)((Q >> 1) & 1), cz = 2 * iz + (int)(Q >> 2);
-        double w[3];
+        T px[8], py[8], pz[8];
+        ld_cell3(cells, g, s, px, py, pz);
+        int n = 0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) w[a] = sizeof(T) == 8 ? g.w[a] : (double)g.wf[a];
-        for (int i = 0; i < kSlots3; ++i) {
-            const T* own = slot3(cells, g, s, i);
-            if (own[0] == (T)kEmpty) break;
-            const double px = (double)own[0], py = (double)own[4], pz = (double)own[8];
-            const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
-            for (int dz = -2; dz <= 2; ++dz)
-                for (int dy = -2; dy <= 2; ++dy)
-                    for (int dx = -2; dx <= 2; ++dx) {
-                        const int nx = ((cx + dx) % g.m[0] + g.m[0]) % g.m[0];
-                        const int ny = ((cy + dy) % g.m[1] + g.m[1]) % g.m[1];
-                        const int nz = ((cz + dz) % g.m[2] + g.m[2]) % g.m[2];
-                        const unsigned sn = sidx3(g, nx, ny, nz);
-                        const double sx = (double)dx * w[0], sy = (double)dy * w[1], sz = (double)dz * w[2];
-                        const float sxf = (float)sx, syf = (float)sy, szf = (float)sz;
-                        for (int j = 0; j < kSlots3; ++j) {
-                            const T* q = slot3(cells, g, sn, j);
-                            if (q[0] == (T)kEmpty) break;
-                            if (dx == 0 && dy == 0 && dz == 0 && j == i) continue;
-                            const float fx = pxf - ((float)q[0] + sxf), fy = pyf - ((float)q[4] + syf),
-                                        fz = pzf - ((float)q[8] + szf);
-                            const float r2f = fx * fx + fy * fy + fz * fz;
-                            if (r2f < lo2f || r2f > hi2f) continue;
-                            const double ex = px - ((double)q[0] + sx), ey = py - ((double)q[4] + sy),
-                                         ez = pz - ((double)q[8] + sz);
-                            const double r2 = (ex * ex + ey * ey) + ez * ez;
-                            if (!(r2 >= edges2[0]) || !(r2 < edges2[kHistBins])) continue;
-                            int lo = 0, hi = kHistBins;   // largest b with edges2[b] <= r2
-                            while (hi - lo > 1) {
-                                const int mid = (lo + hi) >> 1;
-                                if (r2 >= edges2[mid]) lo = mid;
-                                else hi = mid;
-                            }
-                            atomicAdd(&sh[lo], 1u);
-                        }
+        for (int j = 0; j < 8; ++j) n += px[j] != (T)kEmpty;
+        if (n > 0) {
+            double w[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) w[a] = sizeof(T) == 8 ? g.w[a] : (double)g.wf[a];
+#pragma unroll 1
+            for (int k = 0; k < 125; ++k) {
+                const int dx = k % 5 - 2, dy = (k / 5) % 5 - 2, dz = k / 25 - 2;
+                const unsigned sn = sidx3(g, ((cx + dx) % g.m[0] + g.m[0]) % g.m[0],
+                                          ((cy + dy) % g.m[1] + g.m[1]) % g.m[1],
+                                          ((cz + dz) % g.m[2] + g.m[2]) % g.m[2]);
+                T qx[8], qy[8], qz[8];
+                ld_cell3(cells, g, sn, qx, qy, qz);
+                const double sx = (double)dx * w[0], sy = (double)dy * w[1], sz = (double)dz * w[2];
+                const float sxf = (float)sx, syf = (float)sy, szf = (float)sz;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (qx[j] == (T)kEmpty) continue;
+                    const float ex = (float)qx[j] + sxf, ey = (float)qy[j] + syf, ez = (float)qz[j] + szf;
+                    for (int i = 0; i < n; ++i) {
+                        if (k == 62 && j == i) continue;   // the sphere itself (dx = dy = dz = 0)
+                        const T ax = pick8(px, i), ay = pick8(py, i), az = pick8(pz, i);
+                        const float fx = (float)ax - ex, fy = (float)ay - ey, fz = (float)az - ez;
+                        const float r2f = fx * fx + fy * fy + fz * fz;
+                        if (r2f < lo2f || r2f > hi2f) continue;
+                        const double e0 = (double)ax - ((double)qx[j] + sx), e1 = (double)ay - ((double)qy[j] + sy),
+                                     e2 = (double)az - ((double)qz[j] + sz);
+                        hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
                     }
+                }
+            }
         }
     }
     __syncthreads();
