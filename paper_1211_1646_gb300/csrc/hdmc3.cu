@@ -711,8 +711,12 @@ __global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__
 // neighbourhood; a binary32 estimate of r^2 with a wide margin skips pairs
 // far outside [sigma^2, (sigma + 200 dr)^2), the rest are decided in binary64
 // on r^2 = (dx*dx + dy*dy) + dz*dz against the squared bin edges.  One thread
-// per cell: its spheres stay in registers while the 125 neighbour cells are
-// read once each.
+// per cell: its spheres stay in registers while the neighbour cells are read
+// once each.  A cell two steps away along an axis is read only if one of the
+// cell's spheres is within reach of it along that axis (its face is closer
+// than sigma + 200 dr, with a relative margin of 1e-5); with w close to sigma
+// that is rare, so most cells read 27 neighbours instead of 125.  Binary64
+// arithmetic is used only for the pairs the binary32 estimate cannot exclude.
 __device__ __forceinline__ void hist_bin(double r2, const double* __restrict__ edges2, unsigned int* sh) {
     if (!(r2 >= edges2[0]) || !(r2 < edges2[kHistBins])) return;
     int lo = 0, hi = kHistBins;   // largest b with edges2[b] <= r2
@@ -725,7 +729,7 @@ __device__ __forceinline__ void hist_bin(double r2, const double* __restrict__ e
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ cells,
+__global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict__ cells,
                                                    const double* __restrict__ edges2, float lo2f, float hi2f,
                                                    unsigned long long* hist) {
     __shared__ unsigned int sh[kHistBins];
@@ -737,42 +741,64 @@ __global__ void __launch_bounds__(kHistB3) k_hist3(G3 g, const T* __restrict__ c
         const int ix = (int)(r0 % (unsigned)g.h[0]);
         const unsigned r1 = r0 / (unsigned)g.h[0];
         const int iy = (int)(r1 % (unsigned)g.h[1]), iz = (int)(r1 / (unsigned)g.h[1]);
-        const int cx = 2 * ix + (int)(Q & 1), cy = 2 * iy + (int)((Q >> 1) & 1), cz = 2 * iz + (int)(Q >> 2);
+        const int c3[3] = {2 * ix + (int)(Q & 1), 2 * iy + (int)((Q >> 1) & 1), 2 * iz + (int)(Q >> 2)};
         T px[8], py[8], pz[8];
         ld_cell3(cells, g, s, px, py, pz);
         int n = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) n += px[j] != (T)kEmpty;
         if (n > 0) {
-            double w[3];
+            // binary32 widths and the range of offsets per axis
+            float wf[3];
+            int lo[3], hi[3];
+            const float rlim = (float)((g.sigma + (double)kHistBins * kHistDr * g.sigma) * (1.0 + 1.0e-6));
 #pragma unroll
-            for (int a = 0; a < 3; ++a) w[a] = sizeof(T) == 8 ? g.w[a] : (double)g.wf[a];
-#pragma unroll 1
-            for (int k = 0; k < 125; ++k) {
-                const int dx = k % 5 - 2, dy = (k / 5) % 5 - 2, dz = k / 25 - 2;
-                const unsigned sn = sidx3(g, ((cx + dx) % g.m[0] + g.m[0]) % g.m[0],
-                                          ((cy + dy) % g.m[1] + g.m[1]) % g.m[1],
-                                          ((cz + dz) % g.m[2] + g.m[2]) % g.m[2]);
-                T qx[8], qy[8], qz[8];
-                ld_cell3(cells, g, sn, qx, qy, qz);
-                const double sx = (double)dx * w[0], sy = (double)dy * w[1], sz = (double)dz * w[2];
-                const float sxf = (float)sx, syf = (float)sy, szf = (float)sz;
+            for (int a = 0; a < 3; ++a) {
+                wf[a] = g.wf[a];
+                float mn = 3.0e38f, mx = -3.0e38f;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    if (qx[j] == (T)kEmpty) continue;
-                    const float ex = (float)qx[j] + sxf, ey = (float)qy[j] + syf, ez = (float)qz[j] + szf;
-                    for (int i = 0; i < n; ++i) {
-                        if (k == 62 && j == i) continue;   // the sphere itself (dx = dy = dz = 0)
-                        const T ax = pick8(px, i), ay = pick8(py, i), az = pick8(pz, i);
-                        const float fx = (float)ax - ex, fy = (float)ay - ey, fz = (float)az - ez;
-                        const float r2f = fx * fx + fy * fy + fz * fz;
-                        if (r2f < lo2f || r2f > hi2f) continue;
-                        const double e0 = (double)ax - ((double)qx[j] + sx), e1 = (double)ay - ((double)qy[j] + sy),
-                                     e2 = (double)az - ((double)qz[j] + sz);
-                        hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
+                    const float v = (float)(a == 0 ? px[j] : (a == 1 ? py[j] : pz[j]));
+                    if (j < n) {
+                        mn = fminf(mn, v);
+                        mx = fmaxf(mx, v);
                     }
                 }
+                // cell -2 spans [-2w, -w], cell +2 spans [2w, 3w] (margins well
+                // above the binary32 rounding of these bounds)
+                lo[a] = mn + wf[a] < rlim * (1.0f + 1.0e-5f) ? -2 : -1;
+                hi[a] = 2.0f * wf[a] - mx < rlim * (1.0f + 1.0e-5f) ? 2 : 1;
             }
+            const double w0 = sizeof(T) == 8 ? g.w[0] : (double)g.wf[0];
+            const double w1 = sizeof(T) == 8 ? g.w[1] : (double)g.wf[1];
+            const double w2 = sizeof(T) == 8 ? g.w[2] : (double)g.wf[2];
+            for (int dz = lo[2]; dz <= hi[2]; ++dz)
+                for (int dy = lo[1]; dy <= hi[1]; ++dy)
+                    for (int dx = lo[0]; dx <= hi[0]; ++dx) {
+                        const unsigned sn = sidx3(g, wrap3(c3[0] + dx, g.m[0]), wrap3(c3[1] + dy, g.m[1]),
+                                                  wrap3(c3[2] + dz, g.m[2]));
+                        T qx[8], qy[8], qz[8];
+                        ld_cell3(cells, g, sn, qx, qy, qz);
+                        const float sxf = (float)dx * wf[0], syf = (float)dy * wf[1], szf = (float)dz * wf[2];
+                        const bool self = dx == 0 && dy == 0 && dz == 0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (qx[j] == (T)kEmpty) continue;
+                            const float ex = (float)qx[j] + sxf, ey = (float)qy[j] + syf, ez = (float)qz[j] + szf;
+                            for (int i = 0; i < n; ++i) {
+                                if (self && j == i) continue;   // the sphere itself
+                                const T ax = pick8(px, i), ay = pick8(py, i), az = pick8(pz, i);
+                                const float fx = (float)ax - ex, fy = (float)ay - ey, fz = (float)az - ez;
+                                const float r2f = fx * fx + fy * fy + fz * fz;
+                                if (r2f < lo2f || r2f > hi2f) continue;
+                                // the decision, in binary64 as the serial form computes it
+                                const double e0 = (double)ax - ((double)qx[j] + (double)dx * w0);
+                                const double e1 = (double)ay - ((double)qy[j] + (double)dy * w1);
+                                const double e2 = (double)az - ((double)qz[j] + (double)dz * w2);
+                                hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
+                            }
+                        }
+                    }
         }
     }
     __syncthreads();
