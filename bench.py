@@ -87,7 +87,7 @@ def workload():
 SUBSWEEP_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc_subsweep.cuh")
 
 
-SPHERE_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc3.cu")
+SPHERE_SOURCES = ("hdmc_device.cuh", "hdmc_common.cuh", "hdmc3_device.cuh", "hdmc3_subsweep.cuh")
 
 
 def subsweep_source_hash(sources=SUBSWEEP_SOURCES):
