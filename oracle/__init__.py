@@ -59,6 +59,7 @@ def lib():
             "orc_destroy": (None, [vp]),
             "orc_set_move_size": (ctypes.c_int, [vp, ctypes.c_double]),
             "orc_set_balance": (None, [vp, ctypes.c_int, ctypes.c_int]),
+            "orc_set_allow_leave": (ctypes.c_int, [vp, ctypes.c_int]),
             "orc_sweep_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                        _i32p, _i32p, _f64p]),
             "orc_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
@@ -318,6 +319,12 @@ class System:
 
     def set_balance(self, shuffle_particles=True, shuffle_sets=True):
         lib().orc_set_balance(self._h, int(shuffle_particles), int(shuffle_sets))
+
+    def set_allow_leave(self, allow=True):
+        """Negative control of Sec. 2.4 item 1 (binary64 mode, serial): moves
+        that leave the cell are made instead of rejected."""
+        if lib().orc_set_allow_leave(self._h, int(allow)):
+            raise ValueError("allow_leave needs the binary64 mode")
 
     def counters(self):
         out = np.zeros(4, dtype=np.uint64)

@@ -220,6 +220,9 @@ typedef struct oracle {
     uint64_t cnt[4];        /* trials, accepted, rejected (left cell), rejected (overlap) */
     /* balance-control switches (Sec. 2.4): 1 = step performed (default) */
     int shuffle_particles, shuffle_sets;
+    /* negative control of Sec. 2.4 item 1 (binary64 mode only): 1 = a trial
+     * position outside the cell moves the disk into the neighbouring cell */
+    int allow_leave;
 } oracle_t;
 
 static double prev_double(double w) { return nextafter(w, 0.0); }
@@ -481,6 +484,13 @@ void orc_set_balance(oracle_t *o, int shuffle_particles, int shuffle_sets)
     o->shuffle_sets = shuffle_sets;
 }
 
+int orc_set_allow_leave(oracle_t *o, int allow)
+{
+    if (allow && o->prec != 0) return ORC_EINVAL;
+    o->allow_leave = allow;
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sweep-level draws (Alg. 1): set order by Fisher-Yates, shift direction f  */
 /* in {+x,-x,+y,-y}, shift distance d ~ U(0, w/2) along f's axis.            */
@@ -709,8 +719,55 @@ void orc_visit_sequence(int n, int nsel, int32_t *seq)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Negative control of Sec. 2.4 item 1: a disk whose trial position lies     */
+/* outside its cell moves into the neighbouring cell that contains it, if   */
+/* it overlaps no disk of that cell's 3x3 neighbourhood and the cell has a  */
+/* free slot.  It is appended there and removed from its own cell (the      */
+/* remaining slots close up; the cell's visit sequence continues with the   */
+/* new count).  Serial order only.  Returns 1 moved, 0 overlap, 2 no slot.  */
+/* ------------------------------------------------------------------------ */
+static int leave_cell64(oracle_t *o, int cx, int cy, int i, double nx, double ny)
+{
+    int ex = nx < 0.0 ? -1 : (nx >= o->wx ? 1 : 0);
+    int ey = ny < 0.0 ? -1 : (ny >= o->wy ? 1 : 0);
+    double lx = nx - (double)ex * o->wx, ly = ny - (double)ey * o->wy;
+    if (lx < 0.0) lx = 0.0;
+    if (lx >= o->wx) lx = prev_double(o->wx);
+    if (ly < 0.0) ly = 0.0;
+    if (ly >= o->wy) ly = prev_double(o->wy);
+    int dcx = (cx + ex + o->mx) % o->mx, dcy = (cy + ey + o->my) % o->my;
+    int64_t c = (int64_t)cy * o->mx + cx, dc = (int64_t)dcy * o->mx + dcx;
+    if (o->n[dc] >= NMAX) return 2;
+    const double sig2 = o->sigma * o->sigma;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int ncx = (dcx + dx + o->mx) % o->mx, ncy = (dcy + dy + o->my) % o->my;
+            int64_t nc = (int64_t)ncy * o->mx + ncx;
+            for (int j = 0; j < o->n[nc]; ++j) {
+                if (nc == c && j == i) continue;
+                double ddx = lx - (o->X[4 * nc + j] + (double)dx * o->wx);
+                double ddy = ly - (o->Y[4 * nc + j] + (double)dy * o->wy);
+                if (ddx * ddx + ddy * ddy < sig2) return 0;
+            }
+        }
+    int k = o->n[dc]++;
+    o->X[4 * dc + k] = lx;
+    o->Y[4 * dc + k] = ly;
+    for (int j = i; j + 1 < o->n[c]; ++j) {
+        o->X[4 * c + j] = o->X[4 * c + j + 1];
+        o->Y[4 * c + j] = o->Y[4 * c + j + 1];
+    }
+    o->n[c]--;
+    o->X[4 * c + o->n[c]] = EMPTY_SLOT;
+    o->Y[4 * c + o->n[c]] = EMPTY_SLOT;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One cell update of a sub-sweep (Alg. 1, Alg. 2)                          */
 /* ------------------------------------------------------------------------ */
+static int leave_cell64(oracle_t *o, int cx, int cy, int i, double nx, double ny);
+
 static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, uint64_t acc[4])
 {
     int64_t c = (int64_t)cy * o->mx + cx;
@@ -730,7 +787,18 @@ static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
         double nx = X[i] + o->d * U[t];
         double ny = Y[i] + o->d * V[t];
         acc[0]++;
-        if (!(nx >= 0.0 && nx < o->wx && ny >= 0.0 && ny < o->wy)) { acc[2]++; continue; }
+        if (!(nx >= 0.0 && nx < o->wx && ny >= 0.0 && ny < o->wy)) {
+            if (!o->allow_leave) { acc[2]++; continue; }
+            int r = leave_cell64(o, cx, cy, i, nx, ny);
+            if (r == 1) {
+                acc[1]++;
+                n = o->n[c];
+                if (n == 0) break;
+            } else {
+                acc[r == 0 ? 3 : 2]++;
+            }
+            continue;
+        }
         int overlap = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
@@ -809,7 +877,7 @@ static void subsweep(oracle_t *o, uint32_t sweep, int Q)
     int qx = Q & 1, qy = Q >> 1;
     uint64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3)
+#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3) if (!o->allow_leave)
 #endif
     for (int cy = qy; cy < o->my; cy += 2) {
         uint64_t acc[4] = {0, 0, 0, 0};

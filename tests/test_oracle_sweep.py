@@ -235,6 +235,34 @@ def test_two_disks_sample_the_uniform_distribution():
     assert sel.min() > 0.8 * sel.mean() and sel.max() < 1.2 * sel.mean()
 
 
+def test_two_disk_pin_detects_moves_that_leave_the_cell():
+    # Sec. 2.4 item 1: letting a disk leave its cell during a sub-sweep
+    # breaks detailed balance.  The oracle's negative-control switch does
+    # exactly that (the disk moves into the neighbouring cell when it
+    # overlaps nothing there); the two-disk pin above must reject the chain.
+    L = 4.0
+    s = O.System(2, L, L, 1.0, 0.45, 4, 2024, O.FP64, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
+    s.set_allow_leave(True)
+    s.sweep(200)
+    r = []
+    for _ in range(80000):
+        s.sweep(8)
+        xy = s.positions()
+        r.append(math.hypot(_min_image(xy[1, 0] - xy[0, 0], L), _min_image(xy[1, 1] - xy[0, 1], L)))
+    r = np.array(r)
+    assert r.min() >= 1.0 - 1e-12                       # still no overlap
+    ri = r[r < 2.0]
+    crit = 1.6 / math.sqrt(len(ri) / 4)
+    assert stats.kstest((ri**2 - 1) / 3, "uniform").statistic > crit
+    # the separations near contact are under-sampled
+    near = np.mean(ri < 1.2) / ((1.2**2 - 1) / 3)
+    assert near < 0.93
+    c = s.counters()
+    assert c[2] == 0 and c[1] > 0.9 * c[0]              # no move is rejected for leaving
+    with pytest.raises(ValueError):
+        O.System(2, L, L, 1.0, 0.45, 4, 1, O.FP32, xy=np.array([[0.5, 0.5], [2.5, 2.5]])).set_allow_leave(True)
+
+
 def test_tiny_system_matches_rejection_sampling():
     # 4 disks on a 4.4 x 4.4 torus: pair-distance distribution of the Markov
     # chain equals that of independent uniform legal configurations.
