@@ -503,6 +503,30 @@ def oracle_sample(seconds_budget=12.0, threads=None):
     return trials / dt, nt, "%d sweeps + 1 contact histogram + pressure fit of the N=1048576 workload" % sweeps
 
 
+def oracle_sample_spheres(seconds_budget=8.0, threads=None):
+    """The oracle's three-dimensional form, as it stands, on the sphere
+    workload (binary32 mode, all host cores): sweeps + one contact histogram
+    + the pressure fit, until the time budget is used."""
+    import oracle
+    from paper_1211_1646_gb300 import workloads
+    w = workloads.spheres_n1m_phi049("fp32")
+    nt = oracle.set_threads(threads or (os.cpu_count() or 1))
+    s = oracle.System3(w.N, w.L, 1.0, w.d, w.nselect, 1, oracle.FP32)
+    t0 = time.perf_counter()
+    c0 = int(s.counters()[0])
+    sweeps = 0
+    while True:
+        s.sweep(1)
+        sweeps += 1
+        if time.perf_counter() - t0 > seconds_budget * 0.8:
+            break
+    h = s.histogram()
+    oracle.pressure.pressure3(h, 1, w.N, w.L[0] * w.L[1] * w.L[2])
+    dt = time.perf_counter() - t0
+    trials = int(s.counters()[0]) - c0
+    return trials / dt, nt, "%d sweeps + 1 contact histogram + pressure fit of the %d-sphere workload" % (sweeps, w.N)
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the host cores, same workload."""
     import oracle
@@ -570,6 +594,10 @@ def main():
             v, nt, sample = oracle_sample()
             line["cpu_baseline"] = {"value": v, "unit": "trial moves/s", "cores": nt, "kind": "oracle",
                                     "sample": sample}
+            if line.get("spheres"):
+                v3, nt3, sample3 = oracle_sample_spheres()
+                line["spheres"]["cpu_baseline"] = {"value": v3, "unit": "trial moves/s", "cores": nt3,
+                                                   "kind": "oracle", "sample": sample3}
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
