@@ -56,6 +56,7 @@ extern "C" {
 #define HDMC_EOVERLAP 4  /* two disks closer than sigma */
 #define HDMC_ETIMEOUT 5  /* a bounded device wait gave up */
 #define HDMC_ENOMEM 6    /* allocation failed or workspace too small */
+#define HDMC_ECHECK 7    /* a kernel of a checked build computed a cell index outside the grid */
 
 /* ---- precision of the stored coordinates ---- */
 #define HDMC_FP64 0       /* binary64 cell-local offsets; bit-identical to the serial reference */
@@ -468,6 +469,16 @@ void hdmc_destroy(hdmc_t *h);
 
 /* Static description of an error code. */
 const char *hdmc_strerror(int code);
+
+/* Build options of this libhdmc.so: HDMC_BUILD_CHECK when it was compiled
+ * with -DHDMC_CHECK.  Such a build checks every cell index its kernels
+ * compute against the grid; a bad index is replaced by 0 (so no access
+ * leaves the buffer) and sets a bit of the handle's device error word, which
+ * the next synchronising call reports as HDMC_ECHECK.  compute-sanitizer is
+ * not available on every machine; this is its substitute for the kernels'
+ * own index arithmetic.  Normal builds contain none of these checks. */
+#define HDMC_BUILD_CHECK 1
+int hdmc_build_flags(void);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhdmc.so")
+# the bounds-checked debug build (-DHDMC_CHECK), kept apart from the product
+CHECK_DIR = os.path.join(HERE, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libhdmc.so")
 SOURCES = ["hdmc_api.cu", "hdmc_host.cu", "hdmc_batch.cu", "hdmc_draws.cu", "hdmc_f32.cu", "hdmc_f64.cu",
            "hdmc_noalloc.cu", "hdmc3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,21 +41,26 @@ def _inputs():
     return files
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force=False, verbose=False, extra=()):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), check=False):
+    """Builds libhdmc.so (check=True: the -DHDMC_CHECK debug build into
+    _build_check/) and returns its path."""
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if check else (OUT_DIR, LIB)
+    if check:
+        extra = tuple(extra) + ("-DHDMC_CHECK",)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     exe = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [exe] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -66,14 +74,14 @@ def build(force=False, verbose=False, extra=()):
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on " + src)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + [o for _, o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("link of libhdmc.so failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -33,6 +33,7 @@ namespace hdmc {
 
 // Host helpers of the two-dimensional entry points (hdmc_host.cu).
 int cuda_code(cudaError_t e);
+int error_code(unsigned int device_error);
 void bin_axis(double x, double w, int m, int& cell, double& loc);
 double poly_intercept(const std::vector<double>& t, const std::vector<double>& y, int deg);
 void squared_edges(double sigma, double* E);
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kShiftB3) k_shift3(G3 g, const T* __restrict__
             ++k;
         }
     }
-    if (k > kSlots3) atomicOr(&st->error, 1u);
+    if (k > kSlots3) atomicOr(&st->error, kErrOverflow);
     st_cell3(dst, g, s, rx, ry, rz, k >= 4);
     if (s == 0) st->origin[ax] += (double)sd;
 }
@@ -276,7 +277,7 @@ int finish3(hdmc3_t* h) {
     unsigned int err = 0;
     e = cudaMemcpy(&err, &h->st->error, sizeof(err), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_code(e);
-    return err ? HDMC_EOVERFLOW : HDMC_OK;
+    return error_code(err);
 }
 
 bool make_grid3(const double L[3], double sigma, int m[3], double w[3]) {
@@ -629,6 +630,7 @@ int hdmc3_create(hdmc3_t** out, int64_t N, double Lx, double Ly, double Lz, doub
         free3(h);
         return cuda_code(ce);
     }
+    h->g.check = &h->st->error;
     h->lo2f = (float)(E[0] * (1.0 - 1.0e-4));
     h->hi2f = (float)(E[kHistBins] * (1.0 + 1.0e-4));
     h->cur = 0;

@@ -48,6 +48,7 @@ struct G3 {
     int nsel;
     uint32_t key0, key1;
     uint32_t flags;        // kNoParticleShuffle | kNoSetShuffle
+    unsigned int* check;   // builds with -DHDMC_CHECK: device word that collects failed index checks
 };
 
 struct alignas(8) Draw3 {
@@ -66,8 +67,10 @@ struct Dev3 {
 
 __host__ __device__ inline unsigned sidx3(const G3& g, int cx, int cy, int cz) {
     const unsigned q = (unsigned)((cx & 1) + 2 * (cy & 1) + 4 * (cz & 1));
-    return q * g.cq + ((unsigned)(cz >> 1) * (unsigned)g.h[1] + (unsigned)(cy >> 1)) * (unsigned)g.h[0] +
-           (unsigned)(cx >> 1);
+    return (unsigned)checked_cell(g.check,
+                                  q * g.cq + ((unsigned)(cz >> 1) * (unsigned)g.h[1] + (unsigned)(cy >> 1)) *
+                                                 (unsigned)g.h[0] + (unsigned)(cx >> 1),
+                                  g.C);
 }
 
 __device__ __forceinline__ uint32_t factorial8(int n) {

@@ -130,7 +130,7 @@ int check_device(hdmc_t* h) {
     DevState ds;
     int e = read_devstate(h, ds);
     if (e) return e;
-    return (ds.error & 1u) ? HDMC_EOVERFLOW : HDMC_OK;
+    return error_code(ds.error);
 }
 
 // ---- sweep driver ------------------------------------------------------------
@@ -243,6 +243,7 @@ int hdmc_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, dou
     h->shift_table = (SweepDraw*)p;
     p += h->lay.shift_table;
     h->st = (DevState*)p;
+    h->g.check = &h->st->error;
     p += h->lay.state;
     h->partial = (unsigned long long*)p;
     p += h->lay.partial;
@@ -599,7 +600,7 @@ int hdmc_save(hdmc_t* h, void* buf, size_t bytes) {
     if (e) return e;
     DevState ds;
     std::memcpy(&ds, b + L.state, sizeof(ds));
-    return (ds.error & 1u) ? HDMC_EOVERFLOW : HDMC_OK;
+    return error_code(ds.error);
 }
 
 int hdmc_load(hdmc_t* h, const void* buf, size_t bytes) {
@@ -760,15 +761,24 @@ void hdmc_destroy(hdmc_t* h) {
     delete h;
 }
 
+int hdmc_build_flags(void) {
+#ifdef HDMC_CHECK
+    return HDMC_BUILD_CHECK;
+#else
+    return 0;
+#endif
+}
+
 const char* hdmc_strerror(int code) {
     switch (code) {
         case HDMC_OK: return "ok";
         case HDMC_EINVAL: return "invalid argument";
         case HDMC_ECUDA: return "CUDA runtime error";
-        case HDMC_EOVERFLOW: return "more than 4 disks in a cell";
+        case HDMC_EOVERFLOW: return "more disks or spheres in a cell than it has slots";
         case HDMC_EOVERLAP: return "overlapping disks";
         case HDMC_ETIMEOUT: return "bounded device wait timed out";
         case HDMC_ENOMEM: return "out of memory or workspace too small";
+        case HDMC_ECHECK: return "a kernel computed a cell index outside the grid (checked build)";
         default: return "unknown error";
     }
 }

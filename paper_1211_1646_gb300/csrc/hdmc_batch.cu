@@ -140,6 +140,7 @@ int upload_layout(hdmc_batch_t* b, int rows) {
         const Geometry& g = b->sys[r].g;
         ReplicaDesc& d = reps[r];
         d.g = g;
+        d.g.check = &b->sts[r].error;
         d.cell_off = b->cell_off[r];
         d.sub_gx = ceil_div(g.hx, 32);
         d.sub_block0 = sub0;
@@ -243,7 +244,7 @@ int check_batch(hdmc_batch_t* b) {
     e = cuda_code(cudaMemcpy(st.data(), b->sts, sizeof(DevState) * b->R, cudaMemcpyDeviceToHost));
     if (e) return e;
     for (const DevState& s : st)
-        if (s.error & 1u) return HDMC_EOVERFLOW;
+        if (s.error) return error_code(s.error);
     return HDMC_OK;
 }
 
@@ -703,7 +704,7 @@ int hdmc_batch_save(hdmc_batch_t* b, void* buf, size_t bytes) {
     for (int r = 0; r < b->R; ++r) {
         DevState ds;
         std::memcpy(&ds, p + L.states + sizeof(DevState) * (size_t)r, sizeof(ds));
-        if (ds.error & 1u) return HDMC_EOVERFLOW;
+        if (ds.error) return error_code(ds.error);
     }
     return HDMC_OK;
 }

@@ -257,10 +257,10 @@ struct Neighbourhood {
         const int row = (c < 3) ? yd : (c < 5 ? hy : yu);
         // selects, not base[set]: a runtime index would put the array in local memory
         const uint32_t b = (c == 3 || c == 4) ? base[1] : ((c == 1 || c == 6) ? base[2] : base[3]);
-        return b + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col;
+        return (uint32_t)checked_cell(g.check, b + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col, g.C);
     }
     __device__ __forceinline__ uint32_t own(const Geometry& g, int hx, int hy) const {
-        return base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx;
+        return (uint32_t)checked_cell(g.check, base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx, g.C);
     }
 };
 template <typename T>

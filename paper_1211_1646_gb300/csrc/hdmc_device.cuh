@@ -52,7 +52,28 @@ struct Geometry {
     int nsel;              // trial moves per cell and sub-sweep (n_M)
     uint32_t key0, key1;   // Philox key = seed
     uint32_t flags;        // kNoParticleShuffle | kNoSetShuffle (Table 1 controls); 0 = the method
+    unsigned int* check;   // builds with -DHDMC_CHECK: device word that collects failed index checks
 };
+
+// Device error word bits: a cell received more than its slots (bit 0); a
+// computed cell index fell outside the grid (bit 1, builds with -DHDMC_CHECK
+// only, which check every cell index the kernels compute and replace a bad
+// one by 0 so that no access leaves the buffer).
+constexpr uint32_t kErrOverflow = 1u, kErrIndex = 2u;
+
+// Index check of a -DHDMC_CHECK build (no code otherwise).
+__host__ __device__ __forceinline__ long long checked_cell(unsigned int* check, long long idx, long long limit) {
+#if defined(HDMC_CHECK) && defined(__CUDA_ARCH__)
+    if (idx < 0 || idx >= limit) {
+        if (check) atomicOr(check, kErrIndex);
+        return 0;
+    }
+#else
+    (void)check;
+    (void)limit;
+#endif
+    return idx;
+}
 
 // Balance controls of Table 1 (Sec. 2.4): skip the shuffle of the disks of a
 // cell, or take the checkerboard sets in the fixed order 0, 1, 2, 3.  The
@@ -97,7 +118,7 @@ struct ReplicaDesc {
 // This generalises Alg. 3 (even/odd x contiguous) to both axes.
 __host__ __device__ inline long long storage_index(const Geometry& g, int cx, int cy) {
     const int q = (cx & 1) + 2 * (cy & 1);
-    return (long long)q * g.cq + (long long)(cy >> 1) * g.hx + (cx >> 1);
+    return checked_cell(g.check, (long long)q * g.cq + (long long)(cy >> 1) * g.hx + (cx >> 1), g.C);
 }
 
 // ---------------------------------------------------------------------------

@@ -18,6 +18,12 @@ int cuda_code(cudaError_t e) {
     return HDMC_ECUDA;
 }
 
+int error_code(unsigned int device_error) {
+    if (device_error & kErrIndex) return HDMC_ECHECK;
+    if (device_error & kErrOverflow) return HDMC_EOVERFLOW;
+    return HDMC_OK;
+}
+
 // Cell grid of a box: mx = largest even integer <= Lx/sigma (likewise my),
 // w = L/m; needs m >= 4 and w < sqrt(2) sigma (at most 4 disks per cell).
 bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy) {

@@ -27,6 +27,7 @@ struct HostState {
 };
 
 int cuda_code(cudaError_t e);
+int error_code(unsigned int device_error);   // device error word -> HDMC_E* (0: HDMC_OK)
 bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy);
 int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, double dmove, int nselect,
                 uint64_t seed, int precision);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
             }
         }
     }
-    if (kept > 4) atomicOr(&st->error, 1u);
+    if (kept > 4) atomicOr(&st->error, kErrOverflow);
     store_cell(dst + 8 * idx, r);
 }
 

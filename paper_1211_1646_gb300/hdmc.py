@@ -12,7 +12,8 @@ import numpy as np
 
 from . import build as _build
 
-HDMC_OK, HDMC_EINVAL, HDMC_ECUDA, HDMC_EOVERFLOW, HDMC_EOVERLAP, HDMC_ETIMEOUT, HDMC_ENOMEM = range(7)
+HDMC_OK, HDMC_EINVAL, HDMC_ECUDA, HDMC_EOVERFLOW, HDMC_EOVERLAP, HDMC_ETIMEOUT, HDMC_ENOMEM, HDMC_ECHECK = range(8)
+HDMC_BUILD_CHECK = 1
 HDMC_FP64, HDMC_FP32_LOCAL = 0, 1
 HDMC_EMPTY_SLOT = -1.0e4
 HDMC_HIST_BINS = 200
@@ -80,6 +81,7 @@ SIGNATURES = {
     "hdmc_batch_destroy": (None, [_vp]),
     "hdmc_destroy": (None, [_vp]),
     "hdmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "hdmc_build_flags": (ctypes.c_int, []),
     # three dimensions
     "hdmc3_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
@@ -148,6 +150,10 @@ def _precision(p):
 
 def hdmc_strerror(code):
     return lib().hdmc_strerror(code).decode()
+
+
+def hdmc_build_flags():
+    return int(lib().hdmc_build_flags())
 
 
 def hdmc_workspace_bytes(N, Lx, Ly, sigma, precision):
