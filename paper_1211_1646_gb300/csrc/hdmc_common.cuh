@@ -232,11 +232,20 @@ __device__ __forceinline__ void add_block_counters(unsigned int n_tr, unsigned i
 // in set Q^3 (periodic wrap on the half grid).  Directions c = 0..7 run over
 // (dx,dy) = (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1).
 // Cell indices are 32-bit here (the grid has fewer than 2^32 cells) and are
-// widened once, in cell_at.
+// widened once, in cell_at.  Lanes past the end of a row (live = false)
+// compute indices they never use; a -DHDMC_CHECK build checks the live ones.
 struct Neighbourhood {
     uint32_t base[4];   // first cell of set Q, Q^1, Q^2, Q^3
     int xl, xr, yd, yu;
-    __device__ Neighbourhood(const Geometry& g, int Q, int hx, int hy) {
+#ifdef HDMC_CHECK
+    bool live;
+#endif
+    __device__ Neighbourhood(const Geometry& g, int Q, int hx, int hy, bool live_) {
+#ifdef HDMC_CHECK
+        live = live_;
+#else
+        (void)live_;
+#endif
         const int qx = Q & 1, qy = Q >> 1;
         const uint32_t cq = (uint32_t)g.cq;
         base[0] = (uint32_t)Q * cq;
@@ -257,10 +266,18 @@ struct Neighbourhood {
         const int row = (c < 3) ? yd : (c < 5 ? hy : yu);
         // selects, not base[set]: a runtime index would put the array in local memory
         const uint32_t b = (c == 3 || c == 4) ? base[1] : ((c == 1 || c == 6) ? base[2] : base[3]);
-        return (uint32_t)checked_cell(g.check, b + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col, g.C);
+        return checked(g, b + (uint32_t)row * (uint32_t)g.hx + (uint32_t)col);
     }
     __device__ __forceinline__ uint32_t own(const Geometry& g, int hx, int hy) const {
-        return (uint32_t)checked_cell(g.check, base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx, g.C);
+        return checked(g, base[0] + (uint32_t)hy * (uint32_t)g.hx + (uint32_t)hx);
+    }
+    __device__ __forceinline__ uint32_t checked(const Geometry& g, uint32_t i) const {
+#ifdef HDMC_CHECK
+        if (live) return (uint32_t)checked_cell(g.check, i, g.C);
+#else
+        (void)g;
+#endif
+        return i;
     }
 };
 template <typename T>

@@ -67,7 +67,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const int hy = by * ROWS + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
-    const Neighbourhood nbh(g, Q, hx, hy);
+    const Neighbourhood nbh(g, Q, hx, hy, live);
 
     // 1. loads
     Cell<float> own;
@@ -317,7 +317,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
     const int hy = by * ROWS + threadIdx.y;
     const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
-    const Neighbourhood nbh(g, Q, hx, hy);
+    const Neighbourhood nbh(g, Q, hx, hy, live);
 
     Cell<double> own;
 #pragma unroll
