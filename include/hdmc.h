@@ -453,6 +453,23 @@ int hdmc3_set_move_size(hdmc3_t *h, double d);
  * the order 0..7). */
 int hdmc3_set_balance(hdmc3_t *h, int shuffle_particles, int shuffle_sets);
 
+/* Snapshots of a sphere system, as hdmc_snapshot_bytes / hdmc_save /
+ * hdmc_load for disks: a 256-byte header (magic "HDMC3SN1", format version,
+ * precision, N, box, sigma, d, n_M, grid, seed, balance controls, sweep and
+ * shift counters, accumulated sample count), then at 256-byte aligned
+ * offsets the device state (trial counters, grid origin, error word), the
+ * histogram accumulator and the cells in the device layout (primary halves
+ * of all cells, then secondary halves; binary32 or binary64).  Load requires
+ * the same N, box, sigma and precision, takes d, n_M, seed and the balance
+ * controls from the image, and checks the cells on the device before
+ * anything is replaced: a wrong header, an occupied slot after an empty one,
+ * a coordinate outside [0, w), an empty slot not holding HDMC_EMPTY_SLOT in
+ * all three coordinates, or a sphere total other than N gives HDMC_EINVAL
+ * and the handle keeps its state.  Save and load synchronise. */
+size_t hdmc3_snapshot_bytes(const hdmc3_t *h);
+int hdmc3_save(hdmc3_t *h, void *buf, size_t bytes);
+int hdmc3_load(hdmc3_t *h, const void *buf, size_t bytes);
+
 /* Waits for the handle's stream and reports device-side errors. */
 int hdmc3_sync(hdmc3_t *h);
 

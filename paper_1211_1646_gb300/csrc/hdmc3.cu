@@ -244,6 +244,35 @@ __global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict_
         if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
 }
 
+// Check of a cell image (snapshot load): occupied slots form a prefix of
+// each cell (slot 3 occupied before the secondary half is read), occupied
+// coordinates lie in [0, w) on every axis, empty slots hold kEmpty in all
+// three coordinates.  out[0] += spheres, out[1] |= 1 on a bad cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_check3(G3 g, const T* __restrict__ cells, unsigned long long* out) {
+    const unsigned s = blockIdx.x * 256 + threadIdx.x;
+    unsigned n = 0;
+    bool bad = false;
+    if (s < g.C) {
+        T x[8], y[8], z[8];
+        ld_cell3(cells, g, s, x, y, z);
+        bool empty_seen = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (x[j] == (T)kEmpty && y[j] == (T)kEmpty && z[j] == (T)kEmpty) {
+                empty_seen = true;
+            } else {
+                bad |= empty_seen || !(x[j] >= (T)0 && x[j] < Ar3<T>::w(g, 0)) ||
+                       !(y[j] >= (T)0 && y[j] < Ar3<T>::w(g, 1)) || !(z[j] >= (T)0 && z[j] < Ar3<T>::w(g, 2));
+                ++n;
+            }
+        }
+    }
+    const unsigned tot = __reduce_add_sync(0xFFFFFFFFu, n);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(out, (unsigned long long)tot);
+    if (bad) atomicOr(out + 1, 1ull);
+}
+
 }  // namespace hdmc
 
 // ---------------------------------------------------------------------------
@@ -572,9 +601,148 @@ int set_geometry3(G3& g, const double L[3], double sigma, double d, int nselect,
     return HDMC_OK;
 }
 
+// ---- snapshots ------------------------------------------------------------------
+constexpr char kSnap3Magic[8] = {'H', 'D', 'M', 'C', '3', 'S', 'N', '1'};
+constexpr uint32_t kSnap3Version = 1;
+constexpr size_t kSnap3Header = 256;
+
+struct Snap3Header {
+    char magic[8];
+    uint32_t version, precision;
+    int64_t N;
+    double L[3], sigma, d;
+    int32_t nsel, m[3];
+    uint32_t key0, key1, flags, pad;
+    uint64_t sweeps, shifts;
+    int64_t n_samples;
+    uint64_t off_state, off_hist, off_cells, cell_bytes, total;
+};
+static_assert(sizeof(Snap3Header) <= kSnap3Header, "sphere snapshot header");
+
+struct Snap3Layout {
+    size_t state, hist, cells, cell_bytes, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+Snap3Layout snap3_layout(const hdmc3_t* h) {
+    Snap3Layout L;
+    L.state = kSnap3Header;
+    L.hist = L.state + align256(sizeof(Dev3));
+    L.cells = L.hist + align256(sizeof(unsigned long long) * kHistBins);
+    L.cell_bytes = (size_t)h->g.C * kCell3 * h->el;
+    L.total = L.cells + L.cell_bytes;
+    return L;
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t hdmc3_snapshot_bytes(const hdmc3_t* h) { return h ? snap3_layout(h).total : 0; }
+
+int hdmc3_save(hdmc3_t* h, void* buf, size_t bytes) {
+    if (!h || !buf) return HDMC_EINVAL;
+    const Snap3Layout L = snap3_layout(h);
+    if (bytes < L.total) return HDMC_EINVAL;
+    char* b = static_cast<char*>(buf);
+    Snap3Header hd{};
+    std::memcpy(hd.magic, kSnap3Magic, sizeof(kSnap3Magic));
+    hd.version = kSnap3Version;
+    hd.precision = (uint32_t)h->prec;
+    hd.N = h->N;
+    for (int a = 0; a < 3; ++a) {
+        hd.L[a] = h->L[a];
+        hd.m[a] = h->g.m[a];
+    }
+    hd.sigma = h->g.sigma;
+    hd.d = h->g.d;
+    hd.nsel = h->g.nsel;
+    hd.key0 = h->g.key0;
+    hd.key1 = h->g.key1;
+    hd.flags = h->g.flags;
+    hd.sweeps = h->sweeps;
+    hd.shifts = h->shifts;
+    hd.n_samples = h->samples;
+    hd.off_state = L.state;
+    hd.off_hist = L.hist;
+    hd.off_cells = L.cells;
+    hd.cell_bytes = L.cell_bytes;
+    hd.total = L.total;
+    std::memset(b, 0, L.cells);
+    std::memcpy(b, &hd, sizeof(hd));
+    const cudaStream_t s = h->stream;
+    int e = cuda_code(cudaMemcpyAsync(b + L.state, h->st, sizeof(Dev3), cudaMemcpyDeviceToHost, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(b + L.hist, h->hist, sizeof(unsigned long long) * kHistBins,
+                                      cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaMemcpyAsync(b + L.cells, h->cells[h->cur], L.cell_bytes, cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    Dev3 st;
+    std::memcpy(&st, b + L.state, sizeof(st));
+    return error_code(st.error);
+}
+
+int hdmc3_load(hdmc3_t* h, const void* buf, size_t bytes) {
+    if (!h || !buf) return HDMC_EINVAL;
+    const Snap3Layout L = snap3_layout(h);
+    if (bytes < L.total) return HDMC_EINVAL;
+    const char* b = static_cast<const char*>(buf);
+    Snap3Header hd;
+    std::memcpy(&hd, b, sizeof(hd));
+    const G3& g = h->g;
+    bool same = std::memcmp(hd.magic, kSnap3Magic, sizeof(kSnap3Magic)) == 0 && hd.version == kSnap3Version &&
+                hd.precision == (uint32_t)h->prec && hd.N == h->N && hd.sigma == g.sigma &&
+                hd.off_state == L.state && hd.off_hist == L.hist && hd.off_cells == L.cells &&
+                hd.cell_bytes == L.cell_bytes && hd.total == L.total;
+    for (int a = 0; a < 3; ++a) same = same && hd.L[a] == h->L[a] && hd.m[a] == g.m[a];
+    if (!same) return HDMC_EINVAL;
+    if (hd.nsel < 1 || hd.nsel > 255 || hd.n_samples < 0 || (hd.flags & ~(kNoParticleShuffle | kNoSetShuffle)) != 0)
+        return HDMC_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(hd.d > 0) || !(hd.d < 0.5 * g.w[a])) return HDMC_EINVAL;
+    Dev3 st;
+    std::memcpy(&st, b + L.state, sizeof(st));
+    if (st.error != 0) return HDMC_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(st.origin[a])) return HDMC_EINVAL;
+    // cells into the idle half of the double buffer, checked there
+    const cudaStream_t s = h->stream;
+    void* idle = h->cells[1 - h->cur];
+    unsigned long long* res = reinterpret_cast<unsigned long long*>(h->table + kDrawChunk3);  // scratch
+    unsigned long long r[2] = {0, 0};
+    int e = cuda_code(cudaMemcpyAsync(idle, b + L.cells, L.cell_bytes, cudaMemcpyHostToDevice, s));
+    if (!e) e = cuda_code(cudaMemsetAsync(res, 0, 2 * sizeof(unsigned long long), s));
+    if (!e) {
+        const unsigned blocks = (g.C + 255) / 256;
+        if (h->prec == HDMC_FP64) k_check3<double><<<blocks, 256, 0, s>>>(g, (const double*)idle, res);
+        else k_check3<float><<<blocks, 256, 0, s>>>(g, (const float*)idle, res);
+        e = cuda_code(cudaGetLastError());
+    }
+    if (!e) e = cuda_code(cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    if (r[1] != 0 || r[0] != (unsigned long long)h->N) return HDMC_EINVAL;
+    // commit
+    e = cuda_code(cudaMemcpyAsync(h->st, &st, sizeof(Dev3), cudaMemcpyHostToDevice, s));
+    if (!e)
+        e = cuda_code(cudaMemcpyAsync(h->hist, b + L.hist, sizeof(unsigned long long) * kHistBins,
+                                      cudaMemcpyHostToDevice, s));
+    if (!e) e = cuda_code(cudaStreamSynchronize(s));
+    if (e) return e;
+    h->cur = 1 - h->cur;
+    h->g.d = hd.d;
+    h->g.df = (float)hd.d;
+    h->g.nsel = hd.nsel;
+    h->g.key0 = hd.key0;
+    h->g.key1 = hd.key1;
+    h->g.flags = hd.flags;
+    h->sweeps = hd.sweeps;
+    h->shifts = hd.shifts;
+    h->samples = hd.n_samples;
+    return HDMC_OK;
+}
 
 int hdmc3_create(hdmc3_t** out, int64_t N, double Lx, double Ly, double Lz, double sigma, double d, int nselect,
                  uint64_t seed, int precision, const double* xyz, void* stream) {

@@ -98,6 +98,9 @@ SIGNATURES = {
     "hdmc3_set_move_size": (ctypes.c_int, [_vp, ctypes.c_double]),
     "hdmc3_set_balance": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "hdmc3_sync": (ctypes.c_int, [_vp]),
+    "hdmc3_snapshot_bytes": (ctypes.c_size_t, [_vp]),
+    "hdmc3_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "hdmc3_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hdmc3_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
     "hdmc3_destroy": (None, [_vp]),
 }
@@ -726,6 +729,21 @@ def hdmc3_sync(h):
     _check(lib().hdmc3_sync(h), "hdmc3_sync")
 
 
+def hdmc3_snapshot_bytes(h):
+    return int(lib().hdmc3_snapshot_bytes(h))
+
+
+def hdmc3_save(h, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc3_save(h, ptr, n), "hdmc3_save")
+    return buf
+
+
+def hdmc3_load(h, buf):
+    ptr, n = _host_buffer(buf)
+    _check(lib().hdmc3_load(h, ptr, n), "hdmc3_load")
+
+
 def hdmc3_profile_sweeps(h, n):
     """Mean ms per (sub-sweep, shift) launch over n sweeps."""
     a, b = ctypes.c_double(), ctypes.c_double()
@@ -805,6 +823,19 @@ class System3:
 
     def sync(self):
         hdmc3_sync(self.h)
+
+    def snapshot_bytes(self):
+        return hdmc3_snapshot_bytes(self.h)
+
+    def save(self, buf=None):
+        """Snapshot into buf (a host numpy array or CPU tensor, pinned or not;
+        a new uint8 array if None); returns buf."""
+        if buf is None:
+            buf = np.empty(self.snapshot_bytes(), dtype=np.uint8)
+        return hdmc3_save(self.h, buf)
+
+    def load(self, buf):
+        hdmc3_load(self.h, buf)
 
     def profile_sweeps(self, n):
         return hdmc3_profile_sweeps(self.h, n)

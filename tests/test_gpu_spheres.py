@@ -189,3 +189,71 @@ def test_equation_of_state_carnahan_starling(prec):
     print("%s: Z = %.5f +- %.5f, Carnahan-Starling %.5f" % (prec, mean, se, cs))
     assert se < 0.01
     assert abs(mean - cs) < 3 * se + 1e-3 * cs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_snapshot_resume_is_bit_identical(prec):
+    from paper_1211_1646_gb300 import hdmc
+    w = W.spheres_n2048_phi045()
+    a = hdmc.System3(w.N, w.L, 1.0, w.d, 4, 21, prec)
+    a.set_balance(False, True)
+    a.sweep(7)
+    a.shift()
+    a.sample()
+    img = a.save()
+    a.sweep(9)
+    a.sample()
+    # a system of another seed, move and balance takes them from the image
+    b = hdmc.System3(w.N, w.L, 1.0, 0.05, 4, 999, prec)
+    b.load(img)
+    b.sweep(9)
+    b.sample()
+    assert np.array_equal(a.state()[0], b.state()[0])
+    assert np.array_equal(a.counters(), b.counters())
+    assert np.array_equal(a.origin(), b.origin())
+    pa, pb = a.pressure(), b.pressure()
+    assert pa[3] == pb[3] == 2 and np.array_equal(pa[2], pb[2])
+    # and both equal the oracle's straight run
+    o = O.System3(w.N, w.L, 1.0, w.d, 4, 21, PREC[prec])
+    o.set_balance(False, True)
+    o.sweep(7)
+    o.shift()
+    o.sweep(9)
+    assert np.array_equal(a.state()[0], o.state()[0])
+
+
+def test_bad_snapshots_are_rejected_and_state_kept():
+    from paper_1211_1646_gb300 import hdmc
+    w = W.spheres_n2048_phi045()
+    s = hdmc.System3(w.N, w.L, 1.0, w.d, 4, 22, "fp32")
+    s.sweep(3)
+    good = s.save()
+    before = s.state()[0].copy()
+    C = s.C
+    cells = 256 + 256 + ((8 * 200 + 255) // 256) * 256        # header, state, histogram
+    el = 4
+    bad = []
+    x = good.copy(); x[0] ^= 1; bad.append(x)                     # magic
+    x = good.copy(); x[cells:cells + 4] = np.frombuffer(np.float32(5.0).tobytes(), np.uint8); bad.append(x)  # x >= w
+    # a sphere removed: the first occupied slot 0 of some cell made empty in all three coordinates
+    arr = good[cells:cells + C * 12 * el].view(np.float32).reshape(C, 12)
+    k = int(np.argmax(arr[:, 0] >= 0))
+    x = good.copy()
+    v = x[cells:cells + C * 12 * el].view(np.float32).reshape(C, 12)
+    v[k, 0] = v[k, 4] = v[k, 8] = -1.0e4
+    bad.append(x)
+    x = good.copy()
+    v = x[cells:cells + C * 12 * el].view(np.float32).reshape(C, 12)
+    v[k, 1] = 0.5 if v[k, 1] < 0 else v[k, 1]
+    if v[k, 1] >= 0:                                               # slot 1 occupied after an empty slot 0
+        v[k, 0] = v[k, 4] = v[k, 8] = -1.0e4
+        bad.append(x)
+    other = hdmc.System3(4 * 6**3, [9.0] * 3, 1.0, 0.1, 4, 1, "fp32").save()
+    bad.append(other)
+    for img in bad:
+        with pytest.raises(hdmc.HDMCError) as e:
+            s.load(img)
+        assert e.value.code == hdmc.HDMC_EINVAL
+        assert np.array_equal(s.state()[0], before)
+    s.load(good)
+    assert np.array_equal(s.state()[0], before)
