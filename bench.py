@@ -423,9 +423,29 @@ def run_hdmc(args, rank, world, dist):
                                    "frac": ach / hbm_peak, "traffic": profiled_traffic_spheres(),
                                    "kernel": "k_sub3<float>", "peak_kind": peak_kind,
                                    "ms_per_launch": sub3, "algorithmic_bytes_per_launch": bytes3}
+            if prec == "fp32":
+                # end to end through the C ABI with host buffers: every step
+                # loads the snapshot from pinned host memory (H2D), runs the
+                # step (histogram back for the fit) and saves it (D2H)
+                snap = torch.empty(s3.snapshot_bytes(), dtype=torch.uint8, pin_memory=True)
+                s3.save(snap)
+                e2e_t, e2e_s = 0, 0.0
+                torch.cuda.synchronize(dev)
+                for _ in range(max(1, nsteps)):
+                    c0 = int(s3.counters()[0])
+                    t0 = time.perf_counter()
+                    s3.load(snap)
+                    one_step(s3)
+                    s3.save(snap)
+                    e2e_s += time.perf_counter() - t0
+                    e2e_t += int(s3.counters()[0]) - c0
+                e2e_s = max_over_ranks(e2e_s)
+                leg["e2e"] = {"value": sum_over_ranks(e2e_t) / e2e_s, "unit": "trial moves/s",
+                              "h2d_bytes_per_step": snap.numel(), "d2h_bytes_per_step": snap.numel() + 200 * 8}
             spheres[prec] = leg
             s3.close()
         spheres["value"] = spheres["fp32"]["value"]
+        spheres["e2e"] = spheres["fp32"]["e2e"]
 
     launches_per_step = KERNELS_PER_SWEEP * SWEEPS_PER_STEP + math.ceil(SWEEPS_PER_STEP / GRAPH_CHUNK) + 1
     line = {
