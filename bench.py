@@ -129,6 +129,25 @@ def profiled_traffic_spheres():
 # per block and 2 fields per attempt; 9 operations per attempt for the
 # direction (2 fields extracted, converted and scaled; u*u + v*v and its
 # compare); 4/pi attempts per kept direction.
+# ALU work of one binary32 hard-sphere trial move, in 32-bit lane operations
+# (an FMA is one): the direction (Philox4x32-10 at 80 operations per block,
+# two attempts per block; per attempt 12 for three 21-bit fields and their
+# conversion, 4 for the ball test; 6/pi attempts per kept direction); trial
+# position and containment (3 FMAs, 6 compares); the other spheres of the
+# cell (0.37 on average, 7 each); the gathered candidates (12.5 on average at
+# n_M = 4, about 11 tested before a hit ends the scan, 7 each); the cell's
+# gather shared by its n_M = 4 trials (31 occupied neighbour slots at 13
+# each, reach box 20); the shuffle shared likewise (a Philox block and the
+# decode for the 27 % of cells with n >= 2).
+SPHERE_ALU_OPS_PER_TRIAL = {
+    "direction": (80.0 / 2 + 12 + 4) * 6 / math.pi,
+    "trial_and_containment": 9.0,
+    "own_cell": 0.37 * 7,
+    "candidates": 11 * 7.0,
+    "gather": (31 * 13 + 20) / 4.0,
+    "shuffle": 0.27 * 100 / 4.0,
+}
+
 ALU_OPS_PER_TRIAL = {
     "slot_tests": 36 * 5,
     "trial_and_containment": 6,
@@ -423,6 +442,12 @@ def run_hdmc(args, rank, world, dist):
                                    "frac": ach / hbm_peak, "traffic": profiled_traffic_spheres(),
                                    "kernel": "k_sub3<float>", "peak_kind": peak_kind,
                                    "ms_per_launch": sub3, "algorithmic_bytes_per_launch": bytes3}
+                tpl3 = t3 / nsteps / (SWEEPS_PER_STEP * 8)
+                ops3 = sum(SPHERE_ALU_OPS_PER_TRIAL.values())
+                ach3 = ops3 * tpl3 / (sub3 / 1e3) / 1e12
+                leg["roofline_alu"] = {"bound": "alu", "achieved": ach3, "peak": alu_peak, "unit": "Tops/s",
+                                       "frac": ach3 / alu_peak, "kernel": "k_sub3<float>",
+                                       "trials_per_launch": tpl3, "ops_per_trial": ops3}
             if prec == "fp32":
                 # end to end through the C ABI with host buffers: every step
                 # loads the snapshot from pinned host memory (H2D), runs the
