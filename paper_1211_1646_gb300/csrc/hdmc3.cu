@@ -794,6 +794,9 @@ int hdmc3_create(hdmc3_t** out, int64_t N, double Lx, double Ly, double Lz, doub
     double E[kHistBins + 1];
     squared_edges(sigma, E);
     if (ce == cudaSuccess) ce = cudaMemcpy(h->edges2, E, sizeof(E), cudaMemcpyHostToDevice);
+    // the set-up above ran on the legacy default stream: finish it before
+    // work is enqueued on the handle's stream, which need not wait for it
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) {
         free3(h);
         return cuda_code(ce);
@@ -865,7 +868,7 @@ int hdmc3_pressure(hdmc3_t* h, double* betaP_over_rho, double* g_contact, uint64
     int e = finish3(h);
     unsigned long long hh[kHistBins];
     cudaError_t ce = cudaMemcpy(hh, h->hist, sizeof(hh), cudaMemcpyDeviceToHost);
-    if (ce == cudaSuccess) ce = cudaMemset(h->hist, 0, sizeof(hh));
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->hist, 0, sizeof(hh), h->stream);
     if (ce != cudaSuccess) return cuda_code(ce);
     const double sigma = h->g.sigma, dr = kHistDr * sigma, c = kFitRange * sigma;
     const double rho = (double)h->N / (h->L[0] * h->L[1] * h->L[2]);
