@@ -287,6 +287,9 @@ int hdmc_set_positions(hdmc_t* h, const double* xy) {
         ds.origin[0] = ds.origin[1] = 0.0;
         e = cuda_code(cudaMemcpy(h->st, &ds, sizeof(ds), cudaMemcpyHostToDevice));
     }
+    // the copies ran on the legacy default stream: finish them before work is
+    // enqueued on the handle's stream, which need not wait for it
+    if (!e) e = cuda_code(cudaDeviceSynchronize());
     return e;
 }
 
@@ -507,6 +510,7 @@ int hdmc_set_state(hdmc_t* h, const double* local, const uint8_t* counts, const 
     ds.shift_next = shifts_done;
     ds.error = 0;
     e = cuda_code(cudaMemcpy(h->st, &ds, sizeof(ds), cudaMemcpyHostToDevice));
+    if (!e) e = cuda_code(cudaDeviceSynchronize());   // as in hdmc_set_positions
     h->sweeps = sweeps_done;
     h->shifts = shifts_done;
     return e;
