@@ -161,10 +161,15 @@ int upload_layout(hdmc_batch_t* b, int rows) {
         hi.insert(hi.end(), nhi, (unsigned short)r);
         hi0 += nhi;
     }
-    int e = cuda_code(cudaMemcpy(b->reps, reps.data(), sizeof(ReplicaDesc) * R, cudaMemcpyHostToDevice));
+    // kernels already enqueued on the batch's stream read the old descriptors
+    int e = cuda_code(cudaStreamSynchronize(b->stream));
+    if (!e) e = cuda_code(cudaMemcpy(b->reps, reps.data(), sizeof(ReplicaDesc) * R, cudaMemcpyHostToDevice));
     if (!e) e = cuda_code(cudaMemcpy(b->sub_map, sub.data(), sizeof(unsigned short) * sub.size(), cudaMemcpyHostToDevice));
     if (!e) e = cuda_code(cudaMemcpy(b->sh_map, sh.data(), sizeof(unsigned short) * sh.size(), cudaMemcpyHostToDevice));
     if (!e) e = cuda_code(cudaMemcpy(b->hi_map, hi.data(), sizeof(unsigned short) * hi.size(), cudaMemcpyHostToDevice));
+    // the copies ran on the legacy default stream: finish them before work is
+    // enqueued on the batch's stream, which need not wait for it
+    if (!e) e = cuda_code(cudaDeviceSynchronize());
     if (e) return e;
     b->host_reps = reps;
     b->sub_blocks = sub0;
