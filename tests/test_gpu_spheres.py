@@ -257,3 +257,23 @@ def test_bad_snapshots_are_rejected_and_state_kept():
         assert np.array_equal(s.state()[0], before)
     s.load(good)
     assert np.array_equal(s.state()[0], before)
+
+
+def test_side_stream_matches_the_oracle():
+    # a handle on a torch side stream (which does not wait for the legacy
+    # default stream): creation, sweeps, a snapshot round trip, histogram
+    import torch
+    from paper_1211_1646_gb300 import hdmc
+    w = W.spheres_n2048_phi045()
+    side = torch.cuda.Stream()
+    g = hdmc.System3(w.N, w.L, 1.0, w.d, 4, 31, "fp32", stream=side.cuda_stream)
+    o = O.System3(w.N, w.L, 1.0, w.d, 4, 31, O.FP32)
+    g.sweep(6)
+    img = g.save()
+    g.sweep(4)
+    g.load(img)
+    g.sweep(4)
+    o.sweep(10)
+    g.sample()
+    assert np.array_equal(g.state()[0], o.state()[0])
+    assert np.array_equal(g.pressure()[2], o.histogram())
