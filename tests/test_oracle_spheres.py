@@ -158,20 +158,30 @@ def test_shift_is_a_relabelling_3d():
         assert np.abs(_min_image(A - B, L)).max() < 1e-9
 
 
-def test_shift_conserves_spheres_on_cell_edges():
-    # spheres exactly on lower cell corners and just below upper corners
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_shift_conserves_spheres_on_cell_edges(prec):
+    # spheres exactly on lower cell corners and just below upper corners (in
+    # binary32 the upper ones round onto the face and are clamped below it)
     w, n = 1.1, 4
     L = [n * w] * 3
     lo = [[i * w, j * w, k * w] for k in (0, 2) for j in (0, 2) for i in (0, 2)]
     hi = [[(i + 1) * w - 1e-12, (j + 1) * w - 1e-12, (k + 1) * w - 1e-12] for k in (0, 2) for j in (0, 2)
           for i in (0, 2)]
     xyz = np.array(lo + hi)
-    s = O.System3(len(xyz), L, 1.0, 0.3, 4, 14, O.FP64, xyz=xyz)
+    s = O.System3(len(xyz), L, 1.0, 0.3, 4, 14, prec, xyz=xyz)
+    loc, cnt = s.state()
+    wl = s.w if prec == O.FP64 else s.w.astype(np.float32).astype(np.float64)
+    occ = np.arange(8)[None, :] < cnt[:, None]
+    assert all(loc[:, :, a][occ].max() < wl[a] for a in range(3))
     for _ in range(200):
         s.shift()
-    assert s.state()[1].sum() == len(xyz)
+        assert s.state()[1].sum() == len(xyz)
+    loc, cnt = s.state()
+    occ = np.arange(8)[None, :] < cnt[:, None]
+    assert all(loc[:, :, a][occ].max() < wl[a] and loc[:, :, a][occ].min() >= 0 for a in range(3))
     s.sweep(50)
-    assert s.state()[1].sum() == len(xyz) and O.close_pairs3(s.positions(), L, 1.0) == 0
+    rmin = 1.0 if prec == O.FP64 else 1.0 - 1e-6
+    assert s.state()[1].sum() == len(xyz) and O.close_pairs3(s.positions(), s.box(), rmin) == 0
 
 
 def test_thread_count_and_split_runs_do_not_change_results():
