@@ -425,6 +425,13 @@ def test_estimator3_on_model_distribution():
     R, gr = P.g_of_r3(n, 1, 1, 1.0, 1.0, dr)
     g0 = P.contact_value(R, gr, 1.0, g["c"], g["degree"])
     assert abs(g0 / amp - 1) < g["max_relative_bias"]
+    # a second least-squares routine gives the same intercept
+    keep = (R > 1.0) & (R <= 1.0 + g["c"])
+    alt = np.polyval(np.polyfit((R[keep] - 1.0) / g["c"], gr[keep], g["degree"]), 0.0)
+    assert abs(alt - g0) < 1e-9 * amp
+    # and the pressure formula uses it: beta P / rho = 1 + (2 pi / 3) rho g0
+    bp, g0b, _ = P.pressure3(n, 1, 1, 1.0, 1.0, dr, g["c"])
+    assert abs(g0b - g0) < 1e-12 and abs(bp - (1 + 2 * math.pi / 3 * g0)) < 1e-12
 
 
 @pytest.mark.slow
