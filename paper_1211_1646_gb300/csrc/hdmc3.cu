@@ -166,6 +166,20 @@ __device__ __forceinline__ void hist_bin(double r2, const double* __restrict__ e
     atomicAdd(&sh[lo], 1u);
 }
 
+// The binary64 decision for one pair that the binary32 estimate could not
+// exclude: r^2 = (e0*e0 + e1*e1) + e2*e2 with e = p - (q + d w), as the serial
+// form computes it.  Kept out of line so that the compiler cannot evaluate it
+// speculatively for every pair (binary64 is slow on this GPU).
+template <typename T>
+__device__ __noinline__ void hist_pair_exact(T ax, T ay, T az, T qx, T qy, T qz, int dx, int dy, int dz, double w0,
+                                             double w1, double w2, const double* __restrict__ edges2,
+                                             unsigned int* sh) {
+    const double e0 = (double)ax - ((double)qx + (double)dx * w0);
+    const double e1 = (double)ay - ((double)qy + (double)dy * w1);
+    const double e2 = (double)az - ((double)qz + (double)dz * w2);
+    hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict__ cells,
                                                    const double* __restrict__ edges2, float lo2f, float hi2f,
@@ -229,11 +243,7 @@ __global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict_
                                 const float fx = (float)ax - ex, fy = (float)ay - ey, fz = (float)az - ez;
                                 const float r2f = fx * fx + fy * fy + fz * fz;
                                 if (r2f < lo2f || r2f > hi2f) continue;
-                                // the decision, in binary64 as the serial form computes it
-                                const double e0 = (double)ax - ((double)qx[j] + (double)dx * w0);
-                                const double e1 = (double)ay - ((double)qy[j] + (double)dy * w1);
-                                const double e2 = (double)az - ((double)qz[j] + (double)dz * w2);
-                                hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
+                                hist_pair_exact<T>(ax, ay, az, qx[j], qy[j], qz[j], dx, dy, dz, w0, w1, w2, edges2, sh);
                             }
                         }
                     }
