@@ -45,26 +45,35 @@ def integrated_autocorrelation_time(x, c=5.0, min_length=50.0):
     return t
 
 
-def tune_sampling(make_system, candidates, sweeps, every, r_cut=1.4, equilibrate=0):
+def tune_sampling(make_system, candidates, sweeps, every, r_cut=1.4, equilibrate=0, observable=None, sync=None):
     """For each (d, n_M) in candidates: a fresh system make_system(d, n_M),
-    `equilibrate` sweeps, then `sweeps` sweeps sampling the mean psi_6 every
-    `every` sweeps.  Returns a list of dicts (d, nselect, tau_sweeps,
-    seconds_per_sweep, tau_seconds), sorted by tau_seconds (best first)."""
-    import torch
+    `equilibrate` sweeps, then `sweeps` sweeps sampling an observable every
+    `every` sweeps: by default the mean psi_6 of a disk system (the
+    criterion of Sec. 3.3); observable(system) may give any real or complex
+    number instead (e.g. for spheres).  Only the sweeps are timed (sync,
+    default torch.cuda.synchronize, waits for them).  Returns a list of
+    dicts (d, nselect, tau_sweeps, seconds_per_sweep, tau_seconds), sorted
+    by tau_seconds (best first)."""
+    if sync is None:
+        import torch
+        sync = torch.cuda.synchronize
+    if observable is None:
+        def observable(s):
+            return s.psi6(r_cut)[0]
     out = []
     for d, nm in candidates:
         s = make_system(d, nm)
         if equilibrate:
             s.sweep(equilibrate)
         series = []
-        torch.cuda.synchronize()
+        sync()
         t_run = 0.0
         for _ in range(sweeps // every):
             t0 = time.perf_counter()
             s.sweep(every)
-            torch.cuda.synchronize()
+            sync()
             t_run += time.perf_counter() - t0
-            series.append(s.psi6(r_cut)[0])
+            series.append(observable(s))
         tau = integrated_autocorrelation_time(np.array(series)) * every
         sps = t_run / (sweeps // every * every)
         out.append({"d": d, "nselect": nm, "tau_sweeps": tau, "seconds_per_sweep": sps,

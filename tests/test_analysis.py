@@ -38,3 +38,40 @@ def test_short_or_constant_series_is_refused():
         integrated_autocorrelation_time(ar1(0.999, 200, 3))
     with pytest.raises(ValueError):
         autocorrelation(np.ones(10))
+
+
+class _FakeSystem:
+    """A stand-in with an AR(1) observable whose coefficient depends on the
+    move size: larger moves decorrelate faster (and cost the same time)."""
+
+    def __init__(self, d, nselect):
+        self.a = {0.05: 0.95, 0.25: 0.6}[d]
+        self.rng = np.random.default_rng(int(d * 100) + nselect)
+        self.x = 0.0
+        self.closed = False
+
+    def sweep(self, n):
+        for _ in range(n):
+            self.x = self.a * self.x + self.rng.standard_normal()
+
+    def close(self):
+        self.closed = True
+
+
+def test_tune_sampling_ranks_by_autocorrelation_time_with_any_observable():
+    from paper_1211_1646_gb300.analysis import tune_sampling
+    made = []
+
+    def make(d, nm):
+        s = _FakeSystem(d, nm)
+        made.append(s)
+        return s
+
+    res = tune_sampling(make, [(0.05, 4), (0.25, 4)], sweeps=40000, every=1, equilibrate=100,
+                        observable=lambda s: s.x, sync=lambda: None)
+    assert [r["d"] for r in res] == [0.25, 0.05]
+    taus = {r["d"]: r["tau_sweeps"] for r in res}
+    assert abs(taus[0.25] - 4.0) < 0.6 and abs(taus[0.05] - 39.0) < 8.0   # (1 + a)/(1 - a)
+    assert all(s.closed for s in made)
+    assert all(r["seconds_per_sweep"] > 0 and r["tau_seconds"] == r["tau_sweeps"] * r["seconds_per_sweep"]
+               for r in res)
