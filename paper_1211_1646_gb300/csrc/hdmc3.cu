@@ -169,7 +169,7 @@ __device__ __forceinline__ void hist_bin(double r2, const double* __restrict__ e
 // The binary64 decision for one pair that the binary32 estimate could not
 // exclude: r^2 = (e0*e0 + e1*e1) + e2*e2 with e = p - (q + d w), as the serial
 // form computes it.  Kept out of line so that the compiler cannot evaluate it
-// speculatively for every pair (binary64 is slow on this GPU).
+// speculatively for every pair (binary64 is slow on GB300).
 template <typename T>
 __device__ __noinline__ void hist_pair_exact(T ax, T ay, T az, T qx, T qy, T qz, int dx, int dy, int dz, double w0,
                                              double w1, double w2, const double* __restrict__ edges2,

@@ -19,7 +19,7 @@ namespace hdmc {
 // see a disk, so every disk lands in exactly one cell (Sec. 3.2).  A
 // re-expressed value that rounds onto the upper edge is clamped below it.
 // Grid origin O += f*ds (one thread per shift).  Kept out of line so that the
-// widening to binary64, slow on this GPU, stays in that one thread.
+// widening to binary64, slow on GB300, stays in that one thread.
 template <typename T>
 __device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax, T sd) {
     st->origin[ax] += (double)sd;
