@@ -59,3 +59,47 @@ def test_library_has_no_cpu_fallback_symbols(libpath):
     # the product path never reaches the oracle: no oracle symbol in the library
     L = ctypes.CDLL(libpath)
     assert not hasattr(L, "orc_sweep") and not hasattr(L, "orc_create")
+
+
+C_USER = r"""
+#include <stdio.h>
+#include "hdmc.h"
+int main(void) {
+    hdmc_t *h = NULL;
+    hdmc3_t *s = NULL;
+    double bp = 0.0;
+    int e = hdmc_create(&h, 1024, 33.8958, 33.8958, 1.0, 0.15, 4, 1u, HDMC_FP32_LOCAL, NULL, 0, NULL);
+    if (e == HDMC_OK) {
+        hdmc_sweep(h, 10);
+        hdmc_pressure(h, &bp, NULL, NULL, NULL);
+        hdmc_destroy(h);
+    }
+    int e3 = hdmc3_create(&s, 2048, 13.36, 13.36, 13.36, 1.0, 0.1, 4, 1u, HDMC_FP64, NULL, NULL);
+    if (e3 == HDMC_OK) hdmc3_destroy(s);
+    printf("%d %d %d\n", e, e3, hdmc_build_flags());
+    return (e != HDMC_OK && h != NULL) || (e3 != HDMC_OK && s != NULL) ? 3 : 0;   /* *out is NULL on failure */
+}
+"""
+
+
+def test_header_is_plain_c_and_links(libpath, tmp_path):
+    # a C99 caller (pedantic, warnings as errors) compiles and links against
+    # libhdmc.so; the header also compiles as C++.  Run here, where there may
+    # be no GPU, it must fail cleanly with an error code (no crash).
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text(C_USER)
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(libpath)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lhdmc",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-x",
+                           "c++", str(src), "-fsyntax-only"])
+    import torch
+    if torch.cuda.is_available():
+        return
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    e, e3, flags = map(int, r.stdout.split())
+    assert e != 0 and e3 != 0 and flags == 0
