@@ -340,10 +340,11 @@ void hdmc_batch_destroy(hdmc_batch_t *b);
  * its only device scratch is a file-scope array of HDMC_NOALLOC_MAX_BINS
  * 64-bit counters that every GPU which loads the library keeps until the
  * process exits.
- *   dev_local: device, caller-owned, 8*mx*my doubles in the layout of
- *              hdmc_get_state (slot j of canonical cell c = cy*mx + cx at
- *              [(4c+j)*2], [(4c+j)*2+1], cell-local coordinates; a slot is
- *              empty iff its x is negative).  Read only.
+ *   dev_local: device, caller-owned, 16-byte aligned, 8*mx*my doubles in
+ *              the layout of hdmc_get_state (slot j of canonical cell
+ *              c = cy*mx + cx at [(4c+j)*2], [(4c+j)*2+1], cell-local
+ *              coordinates; a slot is empty iff its x is negative, whatever
+ *              the negative value).  Read only.
  *   mx, my:    cell grid (>= 4 each); wx, wy: cell widths used to translate
  *              neighbouring cells (pass the binary32 widths, widened, for a
  *              state of an HDMC_FP32_LOCAL system).
@@ -354,12 +355,16 @@ void hdmc_batch_destroy(hdmc_batch_t *b);
  *              sigma + nbins dr <= 2 min(wx, wy).
  *   hist:      host, nbins counts (output).
  *   stream:    cudaStream_t or NULL (legacy default stream).
- * Errors: HDMC_EINVAL for a size above the maximum or invalid arguments
- * (nothing is launched), HDMC_ECUDA.  Synchronises the stream.
+ * Errors: HDMC_EINVAL for a size above the maximum, a dev_local that is
+ * not 16-byte aligned or other invalid arguments (nothing is launched),
+ * HDMC_ECUDA.  Synchronises the stream.
  * The first call on each device looks up the device address of the scratch
- * array (with that device current); make that first call before any stream
- * capture.  All calls share the array and each call clears it first, so
- * calls that overlap on the GPU (several streams or host threads) race. */
+ * array (with that device current) and keeps it for the life of the
+ * process; that first call must not come while a stream is being captured.
+ * cudaDeviceReset may move the array, so do not use this entry point in a
+ * process that resets a device it has called it on.  All calls share the
+ * array and each call clears it first, so calls that overlap on the GPU
+ * (several streams or host threads) race. */
 #define HDMC_NOALLOC_MAX_BINS 1024
 int hdmc_histogram_noalloc(const double *dev_local, int32_t mx, int32_t my, double wx, double wy, double sigma,
                            int32_t nbins, double dr, uint64_t *hist, void *stream);

@@ -321,10 +321,10 @@ class System:
         lib().orc_set_balance(self._h, int(shuffle_particles), int(shuffle_sets))
 
     def set_allow_leave(self, allow=True):
-        """Negative control of Sec. 2.4 item 1 (binary64 mode, serial): moves
-        that leave the cell are made instead of rejected."""
+        """Negative control of Sec. 2.4 item 1 (either mode, serial order):
+        moves that leave the cell are made instead of rejected."""
         if lib().orc_set_allow_leave(self._h, int(allow)):
-            raise ValueError("allow_leave needs the binary64 mode")
+            raise ValueError("allow_leave failed")
 
     def counters(self):
         out = np.zeros(4, dtype=np.uint64)

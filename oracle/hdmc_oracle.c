@@ -220,8 +220,8 @@ typedef struct oracle {
     uint64_t cnt[4];        /* trials, accepted, rejected (left cell), rejected (overlap) */
     /* balance-control switches (Sec. 2.4): 1 = step performed (default) */
     int shuffle_particles, shuffle_sets;
-    /* negative control of Sec. 2.4 item 1 (binary64 mode only): 1 = a trial
-     * position outside the cell moves the disk into the neighbouring cell */
+    /* negative control of Sec. 2.4 item 1 (both modes, serial order): 1 = a
+     * trial position outside the cell moves the disk into the neighbouring cell */
     int allow_leave;
 } oracle_t;
 
@@ -486,7 +486,6 @@ void orc_set_balance(oracle_t *o, int shuffle_particles, int shuffle_sets)
 
 int orc_set_allow_leave(oracle_t *o, int allow)
 {
-    if (allow && o->prec != 0) return ORC_EINVAL;
     o->allow_leave = allow;
     return ORC_OK;
 }
@@ -763,10 +762,48 @@ static int leave_cell64(oracle_t *o, int cx, int cy, int i, double nx, double ny
     return 1;
 }
 
+/* The same negative control in the binary32 mode: binary32 widths, the
+ * binary32 overlap predicate and binary32 re-expression in the new cell. */
+static int leave_cell32(oracle_t *o, int cx, int cy, int i, float nx, float ny)
+{
+    int ex = nx < 0.0f ? -1 : (nx >= o->wxf ? 1 : 0);
+    int ey = ny < 0.0f ? -1 : (ny >= o->wyf ? 1 : 0);
+    float lx = nx - (float)ex * o->wxf, ly = ny - (float)ey * o->wyf;
+    if (lx < 0.0f) lx = 0.0f;
+    if (lx >= o->wxf) lx = prev_float(o->wxf);
+    if (ly < 0.0f) ly = 0.0f;
+    if (ly >= o->wyf) ly = prev_float(o->wyf);
+    int dcx = (cx + ex + o->mx) % o->mx, dcy = (cy + ey + o->my) % o->my;
+    int64_t c = (int64_t)cy * o->mx + cx, dc = (int64_t)dcy * o->mx + dcx;
+    if (o->n[dc] >= NMAX) return 2;
+    const float sig2 = (float)(o->sigma * o->sigma);
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int ncx = (dcx + dx + o->mx) % o->mx, ncy = (dcy + dy + o->my) % o->my;
+            int64_t nc = (int64_t)ncy * o->mx + ncx;
+            for (int j = 0; j < o->n[nc]; ++j) {
+                if (nc == c && j == i) continue;
+                float ddx = lx - (o->Xf[4 * nc + j] + (float)dx * o->wxf);
+                float ddy = ly - (o->Yf[4 * nc + j] + (float)dy * o->wyf);
+                if (overlap32(ddx, ddy, sig2)) return 0;
+            }
+        }
+    int k = o->n[dc]++;
+    o->Xf[4 * dc + k] = lx;
+    o->Yf[4 * dc + k] = ly;
+    for (int j = i; j + 1 < o->n[c]; ++j) {
+        o->Xf[4 * c + j] = o->Xf[4 * c + j + 1];
+        o->Yf[4 * c + j] = o->Yf[4 * c + j + 1];
+    }
+    o->n[c]--;
+    o->Xf[4 * c + o->n[c]] = (float)EMPTY_SLOT;
+    o->Yf[4 * c + o->n[c]] = (float)EMPTY_SLOT;
+    return 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One cell update of a sub-sweep (Alg. 1, Alg. 2)                          */
 /* ------------------------------------------------------------------------ */
-static int leave_cell64(oracle_t *o, int cx, int cy, int i, double nx, double ny);
 
 static void cell_update64(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, uint64_t acc[4])
 {
@@ -843,7 +880,18 @@ static void cell_update32(oracle_t *o, uint32_t sweep, int Q, int cx, int cy, ui
         float nx = fmaf(df, U[t], X[i]);
         float ny = fmaf(df, V[t], Y[i]);
         acc[0]++;
-        if (!(nx >= 0.0f && nx < o->wxf && ny >= 0.0f && ny < o->wyf)) { acc[2]++; continue; }
+        if (!(nx >= 0.0f && nx < o->wxf && ny >= 0.0f && ny < o->wyf)) {
+            if (!o->allow_leave) { acc[2]++; continue; }
+            int r = leave_cell32(o, cx, cy, i, nx, ny);
+            if (r == 1) {
+                acc[1]++;
+                n = o->n[c];
+                if (n == 0) break;
+            } else {
+                acc[r == 0 ? 3 : 2]++;
+            }
+            continue;
+        }
         int overlap = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;

@@ -25,6 +25,9 @@ __device__ __align__(256) unsigned long long g_noalloc_hist[HDMC_NOALLOC_MAX_BIN
 // Device address of g_noalloc_hist on each device, looked up on the first
 // call made with that device current (host code may not use the array's name
 // as an address: on the host it is only a stand-in for the device symbol).
+// cudaDeviceReset reloads the module, which may move the array: the cached
+// address is then stale, so this entry point is not for processes that reset
+// a device they have used it on.
 void* g_noalloc_ptr[kMaxDevices];
 std::mutex g_noalloc_mu;
 
@@ -43,7 +46,8 @@ int noalloc_scratch(int dev, unsigned long long** out) {
 // binary64 r^2 against the squared bin edges, conservative binary32
 // candidate selection), reading cells in canonical order c = cy*mx + cx with
 // slot j of cell c at local[(4c+j)*2], local[(4c+j)*2+1]; a slot is
-// occupied iff its x is >= 0.
+// occupied iff its x is >= 0, in the own cell and in every neighbour, so an
+// empty slot may hold any negative x.
 __global__ void __launch_bounds__(256)
 k_hist_canonical(const double* __restrict__ local, int mx, int my, double wx, double wy, double sigma, int nbins,
                  double dr, unsigned long long* __restrict__ hist) {
@@ -97,7 +101,9 @@ k_hist_canonical(const double* __restrict__ local, int mx, int my, double wx, do
                 const f2x qx23 = add2(pk(approx_f32(c.x[2]), approx_f32(c.x[3])), pk(sxf, sxf));
                 const f2x qy01 = add2(pk(approx_f32(c.y[0]), approx_f32(c.y[1])), pk(syf, syf));
                 const f2x qy23 = add2(pk(approx_f32(c.y[2]), approx_f32(c.y[3])), pk(syf, syf));
-                uint32_t cand = 0;
+                uint32_t cand = 0, nocc = 0;   // nocc: occupied slots j of the neighbour, bits 4i + j
+#pragma unroll
+                for (int j = 0; j < 4; ++j) nocc |= c.x[j] >= 0.0 ? (0x1111u << j) : 0u;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const f2x tx2 = pk(ox[i], ox[i]), ty2 = pk(oy[i], oy[i]);
@@ -106,7 +112,7 @@ k_hist_canonical(const double* __restrict__ local, int mx, int my, double wx, do
                     z = zpair(tx2, ty2, qx23, qy23, nt);
                     cand |= ((lo32(z) >> 31) << (4 * i + 2)) | ((hi32(z) >> 31) << (4 * i + 3));
                 }
-                cand &= occupied;
+                cand &= occupied & nocc;
                 if (dx == 0 && dy == 0) cand &= ~0x8421u;
                 while (cand) {
                     const int b = __ffs(cand) - 1;
@@ -140,6 +146,8 @@ extern "C" int hdmc_histogram_noalloc(const double* dev_local, int32_t mx, int32
                                       double sigma, int32_t nbins, double dr, uint64_t* hist, void* stream) {
     using namespace hdmc;
     if (!dev_local || !hist) return HDMC_EINVAL;
+    // the kernel reads the cells with 16-byte loads
+    if ((uintptr_t)dev_local % 16 != 0) return HDMC_EINVAL;
     if (nbins < 1 || nbins > HDMC_NOALLOC_MAX_BINS) return HDMC_EINVAL;
     if (mx < 4 || my < 4 || !(sigma > 0) || !(dr > 0) || !(wx > 0) || !(wy > 0)) return HDMC_EINVAL;
     // two rings of cells must reach the largest distance counted

@@ -197,12 +197,21 @@ def _min_image(d, L):
     return d - L * np.round(d / L)
 
 
-def test_two_disks_sample_the_uniform_distribution():
+# Smallest separation the binary32 chain may produce: its overlap test is
+# fma(dx, dx, fma(dy, dy, -sigma^2)) < 0 on binary32 cell-local coordinates,
+# whose rounding (a few ulp of sigma^2 = 1) admits pairs a hair inside sigma.
+R_MIN = {O.FP64: 1.0 - 1e-12, O.FP32: 1.0 - 1e-6}
+
+
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_two_disks_sample_the_uniform_distribution(prec):
     # Detailed balance (Sec. 2.3) makes the uniform measure on legal
     # configurations stationary: the separation of two disks on a 4x4 torus
-    # is uniform over the square [-2,2)^2 minus the disk |r| < sigma.
+    # is uniform over the square [-2,2)^2 minus the disk |r| < sigma.  Both
+    # arithmetic modes of the oracle must sample it.
     L = 4.0
-    s = O.System(2, L, L, 1.0, 0.45, 4, 2024, O.FP64, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
+    s = O.System(2, L, L, 1.0, 0.45, 4, 2024, prec, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
+    assert s.box() == (L, L)
     s.sweep(200)
     seps = []
     for _ in range(40000):
@@ -211,7 +220,7 @@ def test_two_disks_sample_the_uniform_distribution():
         seps.append([_min_image(xy[1, 0] - xy[0, 0], L), _min_image(xy[1, 1] - xy[0, 1], L)])
     seps = np.array(seps)
     r = np.hypot(seps[:, 0], seps[:, 1])
-    assert r.min() >= 1.0 - 1e-12
+    assert r.min() >= R_MIN[prec]
     inside = r < 2.0
     p_in = 3 * math.pi / (16 - math.pi)
     # correlated samples: allow for an effective sample size of a quarter
@@ -235,13 +244,15 @@ def test_two_disks_sample_the_uniform_distribution():
     assert sel.min() > 0.8 * sel.mean() and sel.max() < 1.2 * sel.mean()
 
 
-def test_two_disk_pin_detects_moves_that_leave_the_cell():
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_two_disk_pin_detects_moves_that_leave_the_cell(prec):
     # Sec. 2.4 item 1: letting a disk leave its cell during a sub-sweep
     # breaks detailed balance.  The oracle's negative-control switch does
     # exactly that (the disk moves into the neighbouring cell when it
-    # overlaps nothing there); the two-disk pin above must reject the chain.
+    # overlaps nothing there); the two-disk pin above must reject the chain,
+    # in both arithmetic modes.
     L = 4.0
-    s = O.System(2, L, L, 1.0, 0.45, 4, 2024, O.FP64, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
+    s = O.System(2, L, L, 1.0, 0.45, 4, 2024, prec, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
     s.set_allow_leave(True)
     s.sweep(200)
     r = []
@@ -250,7 +261,7 @@ def test_two_disk_pin_detects_moves_that_leave_the_cell():
         xy = s.positions()
         r.append(math.hypot(_min_image(xy[1, 0] - xy[0, 0], L), _min_image(xy[1, 1] - xy[0, 1], L)))
     r = np.array(r)
-    assert r.min() >= 1.0 - 1e-12                       # still no overlap
+    assert r.min() >= R_MIN[prec]                       # still no overlap
     ri = r[r < 2.0]
     crit = 1.6 / math.sqrt(len(ri) / 4)
     assert stats.kstest((ri**2 - 1) / 3, "uniform").statistic > crit
@@ -259,13 +270,14 @@ def test_two_disk_pin_detects_moves_that_leave_the_cell():
     assert near < 0.93
     c = s.counters()
     assert c[2] == 0 and c[1] > 0.9 * c[0]              # no move is rejected for leaving
-    with pytest.raises(ValueError):
-        O.System(2, L, L, 1.0, 0.45, 4, 1, O.FP32, xy=np.array([[0.5, 0.5], [2.5, 2.5]])).set_allow_leave(True)
 
 
-def test_tiny_system_matches_rejection_sampling():
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_tiny_system_matches_rejection_sampling(prec):
     # 4 disks on a 4.4 x 4.4 torus: pair-distance distribution of the Markov
-    # chain equals that of independent uniform legal configurations.
+    # chain equals that of independent uniform legal configurations.  With
+    # cells of width 1.1, two disks share a cell often enough that a wrong
+    # own-cell exclusion or visit order shows up here.
     L = 4.4
     rng = np.random.default_rng(8)
     ref = []
@@ -275,14 +287,20 @@ def test_tiny_system_matches_rejection_sampling():
         if min(ds) >= 1.0:
             ref.append(min(ds))
     start = np.array([[0.5, 0.5], [2.7, 0.5], [0.5, 2.7], [2.7, 2.7]])
-    s = O.System(4, L, L, 1.0, 0.4, 4, 77, O.FP64, xy=start)
+    s = O.System(4, L, L, 1.0, 0.4, 4, 77, prec, xy=start)
+    Lx, Ly = s.box()   # binary32 mode: 4 x float(1.1), a hair above 4.4
     s.sweep(200)
     mc = []
+    shared = 0
     for _ in range(15000):
         s.sweep(6)
         xy = s.positions()
-        ds = [math.hypot(*_min_image(xy[i] - xy[j], L)) for i in range(4) for j in range(i + 1, 4)]
+        ds = [math.hypot(_min_image(xy[i, 0] - xy[j, 0], Lx), _min_image(xy[i, 1] - xy[j, 1], Ly))
+              for i in range(4) for j in range(i + 1, 4)]
         mc.append(min(ds))
+        shared += int((s.state()[1] > 1).any())
+    assert min(mc) >= R_MIN[prec]
+    assert shared > 300   # configurations with two disks in one cell are sampled (about 3 %)
     res = stats.ks_2samp(np.array(ref), np.array(mc))
     n_eff = 15000 / 3
     crit = 1.95 * math.sqrt((1 / n_eff) + (1 / len(ref)))
@@ -382,7 +400,8 @@ def test_pressure_formula_closed_form():
 
 
 @pytest.mark.slow
-def test_low_density_virial_series():
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32])
+def test_low_density_virial_series(prec):
     # beta P / rho = 1 + B2 rho + B3 rho^2 + B4 rho^3 + ... for hard disks:
     # B2 = pi sigma^2/2, B3/B2^2 = 4/3 - sqrt(3)/pi, B4/B2^3 = 2 - 9 sqrt(3)/(2 pi) + 10/pi^2.
     phi = 0.10
@@ -394,7 +413,8 @@ def test_low_density_virial_series():
     B4 = B2**3 * (2 - 9 * math.sqrt(3) / (2 * math.pi) + 10 / math.pi**2)
     B5 = B2**4 * 0.3335
     series = 1 + B2 * rho + B3 * rho**2 + B4 * rho**3 + B5 * rho**4
-    s = O.System(N, Lx, Ly, 1.0, 0.45, 4, 31, O.FP64)
+    s = O.System(N, Lx, Ly, 1.0, 0.45, 4, 31, prec)
+    area = s.box()[0] * s.box()[1]
     s.sweep(300)
     blocks = []
     for b in range(20):
@@ -402,7 +422,7 @@ def test_low_density_virial_series():
         for k in range(250):
             s.sweep(2)
             h += s.histogram(200, 1e-4)
-        blocks.append(P.pressure(h, 250, N, Lx * Ly)[0])
+        blocks.append(P.pressure(h, 250, N, area)[0])
     blocks = np.array(blocks)
     mean, se = blocks.mean(), blocks.std(ddof=1) / math.sqrt(len(blocks))
     assert abs(mean - series) < 3 * se + 1e-3, (mean, se, series)
