@@ -24,7 +24,11 @@
  *   prec 0 (FP64): positions are binary64 cell-local offsets.
  *   prec 1 (FP32): positions are binary32 cell-local offsets (the paper stores
  *                  single-precision coordinates, Sec. 5); the cell widths used
- *                  inside the sweep are the binary32 roundings of wx, wy.
+ *                  inside the sweep are the binary32 roundings of wx, wy.  The
+ *                  grid shift alone is evaluated in binary64 (translation,
+ *                  ownership test and re-expression, on the binary32 widths)
+ *                  and rounded to binary32 once, when it is stored; the grid
+ *                  origin accumulates the binary64 shift distance.
  *
  * Readings of the paper taken here (each one is listed in the design notes):
  *  - a cell is the half-open square [0,wx) x [0,wy) in its own frame (Alg. 4
@@ -938,6 +942,17 @@ static void subsweep(oracle_t *o, uint32_t sweep, int Q)
     o->cnt[0] += t0; o->cnt[1] += t1; o->cnt[2] += t2; o->cnt[3] += t3;
 }
 
+/* binary32 value stored for a remapped binary64 coordinate v >= 0 of a cell
+ * of binary32 width wf: v rounded to nearest, clamped below wf (a value just
+ * under the edge may round onto it). */
+static float store32(double v, float wf)
+{
+    float f = (float)v;
+    if (f >= wf) f = prev_float(wf);
+    if (f < 0.0f) f = 0.0f;
+    return f;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Cell shift (Alg. 4): translate every disk by -f*ds.  New cell c keeps the */
 /* disks of old c that stay inside it (old slot order), then takes the disks */
@@ -993,10 +1008,14 @@ static int shift_cells(oracle_t *o, int fdir, double ds)
         o->X = NX; o->Y = NY;
         if (ax) o->Oy += sd; else o->Ox += sd;
     } else {
-        float w = ax ? o->wyf : o->wxf;
-        float dsf = (float)ds;
-        float sd = (float)sgn * dsf;
-        float sw = (float)sgn * w;
+        /* binary32 positions, binary64 remap: the translation x - sd and the
+         * ownership test are evaluated in binary64 on the binary32 cell
+         * width W (exact in binary64), and only the result is rounded to
+         * binary32 (then clamped below the cell's upper edge) */
+        float wf = ax ? o->wyf : o->wxf;
+        double W = (double)wf;
+        double sd = (double)sgn * ds;
+        double sW = (double)sgn * W;
         float *NX = (float *)malloc(sizeof(float) * 4 * (size_t)C);
         float *NY = (float *)malloc(sizeof(float) * 4 * (size_t)C);
         for (int cy = 0; cy < o->my; ++cy)
@@ -1009,18 +1028,17 @@ static int shift_cells(oracle_t *o, int fdir, double ds)
                 int k = 0;
                 for (int j = 0; j < o->n[c]; ++j) {
                     float px = o->Xf[4 * c + j], py = o->Yf[4 * c + j];
-                    float dp = (ax ? py : px) - sd;
-                    if (dp >= 0.0f && dp < w) {
-                        ox[k] = ax ? px : dp; oy[k] = ax ? dp : py; k++;
+                    double dp = (double)(ax ? py : px) - sd;
+                    if (dp >= 0.0 && dp < W) {
+                        float v = store32(dp, wf);
+                        ox[k] = ax ? px : v; oy[k] = ax ? v : py; k++;
                     }
                 }
                 for (int j = 0; j < o->n[nb]; ++j) {
                     float px = o->Xf[4 * nb + j], py = o->Yf[4 * nb + j];
-                    float dp = (ax ? py : px) - sd;
-                    if (!(dp >= 0.0f && dp < w)) {
-                        float v = dp + sw;
-                        if (v >= w) v = prev_float(w);
-                        if (v < 0.0f) v = 0.0f;
+                    double dp = (double)(ax ? py : px) - sd;
+                    if (!(dp >= 0.0 && dp < W)) {
+                        float v = store32(dp + sW, wf);
                         ox[k] = ax ? px : v; oy[k] = ax ? v : py; k++;
                     }
                 }
@@ -1033,7 +1051,7 @@ static int shift_cells(oracle_t *o, int fdir, double ds)
             }
         free(o->Xf); free(o->Yf);
         o->Xf = NX; o->Yf = NY;
-        if (ax) o->Oy += (double)sd; else o->Ox += (double)sd;
+        if (ax) o->Oy += sd; else o->Ox += sd;
     }
     free(o->n);
     o->n = nn;

@@ -134,6 +134,34 @@ def test_shift_is_a_relabelling():
         assert np.abs(d).max() < tol
 
 
+def test_binary32_shift_rounds_each_coordinate_once():
+    # Alg. 4 translates every disk by -f*ds.  In the binary32 mode the
+    # translation, the ownership test and the re-expression in the new cell
+    # are binary64, and only the stored result is rounded to binary32: each
+    # shift moves a disk's global position by at most half an ulp of its new
+    # binary32 local coordinate (plus the binary64 rounding of O + cell*w +
+    # local).  A binary32 remap rounds a migrant twice (x - ds, then + w) and
+    # breaks this bound.
+    w = W.n1024_phi070()
+    s = O.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 3, O.FP32)
+    s.sweep(10)
+    Lx, Ly = s.box()
+    worst = 0.0
+    for _ in range(60):
+        a = s.positions()
+        s.shift()
+        b = s.positions()
+        loc, cnt = s.state()
+        bl = loc[np.arange(4)[None, :] < cnt[:, None]]       # canonical order, like positions()
+        ia, ib = np.lexsort((a[:, 1], a[:, 0])), np.lexsort((b[:, 1], b[:, 0]))
+        d = a[ia] - b[ib]
+        d -= np.array([Lx, Ly]) * np.round(d / [Lx, Ly])
+        half = 0.5 * np.spacing(bl[ib].astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(d) <= half + 1e-12)
+        worst = max(worst, float((np.abs(d) / (half + 1e-300)).max()))
+    assert worst > 0.5   # the bound is approached, so the test has teeth
+
+
 def test_shift_conserves_particles_on_cell_edges():
     # disks sitting exactly on, or one ulp inside, cell edges
     L = 12.0
