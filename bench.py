@@ -120,15 +120,6 @@ def profiled_traffic_spheres():
     return profiled_traffic("subsweep3_f32_n1m.md", SPHERE_SOURCES)
 
 
-# ALU work of one binary32 trial move (Alg. 2), in 32-bit lane operations
-# (an FMA is one operation): the trial position against the 36 slots of the
-# 3x3 cell neighbourhood at 5 operations each (2 differences, 2 FMAs, 1
-# compare); trial coordinate and containment test, 2 FMAs and 4 compares;
-# the random stream, Philox4x32-10 at 8 operations per round (2 wide
-# multiplies = 4, 2 three-input XORs, 2 key additions) with 6 21-bit fields
-# per block and 2 fields per attempt; 9 operations per attempt for the
-# direction (2 fields extracted, converted and scaled; u*u + v*v and its
-# compare); 4/pi attempts per kept direction.
 # ALU work of one binary32 hard-sphere trial move, in 32-bit lane operations
 # (an FMA is one): the direction (Philox4x32-10 at 80 operations per block,
 # two attempts per block; per attempt 12 for three 21-bit fields and their
@@ -148,14 +139,37 @@ SPHERE_ALU_OPS_PER_TRIAL = {
     "shuffle": 0.27 * 100 / 4.0,
 }
 
-ALU_OPS_PER_TRIAL = {
-    "slot_tests": 36 * 5,
-    "trial_and_containment": 6,
-    "philox": 80 * (4 / math.pi) / 3,
-    "directions": 9 * (4 / math.pi),
-}
+# ALU work of one binary32 disk trial move (Alg. 2), the method's own: the
+# trial position against every other disk of the 3x3 cell neighbourhood, 5
+# operations each (2 differences, 2 FMAs, 1 compare), for the mean number of
+# such disks measured from the cell counts (live_candidates); trial coordinate and containment test, 2
+# FMAs and 4 compares; the random stream, Philox4x32-10 at 80 operations per
+# block (10 rounds of 2 wide multiplies = 4, 2 three-input XORs, 2 key
+# additions) with 6 21-bit fields per block and 2 fields per attempt; 9
+# operations per attempt for the direction (2 fields extracted, converted and
+# scaled; u*u + v*v and its compare); 4/pi attempts per kept direction.
+def alu_ops_per_trial(live_candidates):
+    return {
+        "candidate_tests": 5 * live_candidates,
+        "trial_and_containment": 6,
+        "philox": 80 * (4 / math.pi) / 3,
+        "directions": 9 * (4 / math.pi),
+    }
+
+
 LANES_PER_SM = 128      # 32-bit ALU/FMA lanes per SM (4 partitions x 32)
 MAX_SM_MHZ = 2070.0     # GB300 maximum SM clock
+
+
+def live_candidates(sysm):
+    """Mean number of other disks in the 3x3 cell neighbourhood of a disk
+    (the overlap candidates of a trial move), from the system's cell counts:
+    sum over disks of (disks in the 9 cells - 1) / N."""
+    import numpy as np
+    _, cnt = sysm.state()
+    n = cnt.astype(np.int64).reshape(sysm.my, sysm.mx)
+    nine = sum(np.roll(np.roll(n, dy, 0), dx, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    return float((n * (nine - 1)).sum() / n.sum())
 
 
 def load_peaks():
@@ -320,18 +334,24 @@ def run_hdmc(args, rank, world, dist):
     value = trials_all / (ms_max / 1e3)
     clocks = sampler.summary()
 
-    # kernel-level times on the same stream (direct launches with CUDA events)
-    ms_sub, ms_shift, ms_draw = hdmc.hdmc_profile_sweeps(s32.h, 20)
+    # kernel-level times inside recorded graphs, as in the timed step (the
+    # sub-sweeps of 128 sweeps without shifts, then 128 shifts), on the same
+    # stream with CUDA events; and one launch at a time for comparison
+    live = live_candidates(s32)
+    ms_sub, ms_shift = hdmc.hdmc_profile_stages(s32.h, 128)
+    ms_sub_iso, ms_shift_iso, ms_draw = hdmc.hdmc_profile_sweeps(s32.h, 20)
     hbm_peak, peak_kind = load_peaks()
     # algorithmic bytes of one sub-sweep launch: every live particle read once
-    # (the halos of the active cells cover the grid) + the active set's
-    # particles written once: 1.25 * N * 8 B (binary32 offsets)
-    bytes_sub = 1.25 * w.N * 8
+    # (the halos of the active cells cover the grid) and the active set's
+    # particles written once, 1.25 N x 8 B (binary32 offsets), plus the
+    # occupancy count of every cell, C x 1 B
+    bytes_sub = 1.25 * w.N * 8 + s32.mx * s32.my
     achieved_hbm = bytes_sub / (ms_sub / 1e3) / 1e9
     # ALU roofline: the state (8 floats per cell, 37 MB) stays in L2 through
     # a step, and the sub-sweep is bound by the lane-operation rate
     trials_per_launch = trials / args.steps / (SWEEPS_PER_STEP * 4)
-    ops_per_trial = sum(ALU_OPS_PER_TRIAL.values())
+    alu_ops = alu_ops_per_trial(live)
+    ops_per_trial = sum(alu_ops.values())
     achieved_alu = ops_per_trial * trials_per_launch / (ms_sub / 1e3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks.get("sm_max_mhz") or MAX_SM_MHZ
@@ -365,7 +385,7 @@ def run_hdmc(args, rank, world, dist):
     t64, ms64, _ = timed_steps(s64, args.fp64_steps, 1)
     ms64 = max_over_ranks(ms64)
     value64 = sum_over_ranks(t64) / (ms64 / 1e3)
-    ms_sub64, ms_shift64, _ = hdmc.hdmc_profile_sweeps(s64.h, 2)
+    ms_sub64, ms_shift64 = hdmc.hdmc_profile_stages(s64.h, 8)
     s64.close()
 
     # ---- N = 2048^2 at the four densities of that workload (state larger than L2) ----
@@ -377,12 +397,14 @@ def run_hdmc(args, rank, world, dist):
             s4 = hdmc.System(w4.N, w4.Lx, w4.Ly, 1.0, w4.d, w4.nselect, seed, "fp32", device=dev)
             t4, ms4, _ = timed_steps(s4, args.steps, max(1, args.warmup))
             ms4 = max_over_ranks(ms4)
-            sub4, shift4, _ = hdmc.hdmc_profile_sweeps(s4.h, 8)
-            bytes4 = 1.25 * w4.N * 8
+            sub4, shift4 = hdmc.hdmc_profile_stages(s4.h, 64)
+            bytes4 = 1.25 * w4.N * 8 + s4.mx * s4.my
+            bytes4_shift = 2 * w4.N * 8 + 2 * s4.mx * s4.my
             n4m["%.3f" % phi] = {
                 "value": sum_over_ranks(t4) / (ms4 / 1e3), "unit": "trial moves/s",
                 "ms_per_step": ms4 / args.steps, "subsweep_ms": sub4, "shift_ms": shift4,
-                "roofline_hbm_frac": bytes4 / (sub4 / 1e3) / 1e9 / hbm_peak}
+                "roofline_hbm_frac": bytes4 / (sub4 / 1e3) / 1e9 / hbm_peak,
+                "shift_roofline_hbm_frac": bytes4_shift / (shift4 / 1e3) / 1e9 / hbm_peak}
             s4.close()
 
     # ---- 64 batched replicas of uneven N and phi in one launch per stage ----
@@ -407,9 +429,20 @@ def run_hdmc(args, rank, world, dist):
             ms_b += e0.elapsed_time(e1)
         tb = int(b.counters()[:, 0].sum()) - c0
         ms_b = max_over_ranks(ms_b)
+        n_total = sum(r.N for r in reps)
+        c_total = sum(int(gr["mx"]) * int(gr["my"]) for gr in b.grids)
+        # whole-step roofline: per sweep every disk is read once per sub-sweep
+        # and written once, the shift reads and writes it once, and the counts
+        # are read 5 times and written once: 6 N x 8 B + 6 C x 1 B
+        bytes_step = SWEEPS_PER_STEP * (6 * n_total * 8 + 6 * c_total)
+        ach_b = bytes_step / (ms_b / args.steps / 1e3) / 1e9
         batch = {"value": sum_over_ranks(tb) / (ms_b / 1e3), "unit": "trial moves/s",
-                 "ms_per_step": ms_b / args.steps, "replicas": len(reps), "N_total": sum(r.N for r in reps),
+                 "disk_sweeps_per_s": n_total * SWEEPS_PER_STEP / (ms_b / args.steps / 1e3),
+                 "ms_per_step": ms_b / args.steps, "replicas": len(reps), "N_total": n_total,
                  "rows_per_block": rows, "nselect": nm,
+                 "roofline_step": {"bound": "hbm", "achieved": ach_b, "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": ach_b / hbm_peak, "peak_kind": peak_kind,
+                                   "algorithmic_bytes_per_step": bytes_step},
                  "workload": "64 replicas, N log-uniform in [4096, 262144], phi uniform in [0.60, 0.74], "
                              "d = 0.08, autotuned (16 sweeps per candidate)"}
         b.close()
@@ -499,13 +532,20 @@ def run_hdmc(args, rank, world, dist):
                      "frac": achieved_hbm / hbm_peak, "traffic": profiled_traffic(), "kernel": "k_subsweep_f32",
                      "traffic_note": "ncu dram bytes per launch inside a run of sweeps (no cache flush)",
                      "peak_kind": peak_kind, "ms_per_launch": ms_sub,
+                     "ms_per_launch_note": "in-step: mean over the sub-sweep launches of recorded graphs",
                      "algorithmic_bytes_per_launch": bytes_sub},
         "roofline_alu": {"bound": "alu", "achieved": achieved_alu, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved_alu / alu_peak, "kernel": "k_subsweep_f32",
                          "peak_kind": "derived: %d SMs x %d lanes x %.0f MHz" % (sms, LANES_PER_SM, mhz),
-                         "trials_per_launch": trials_per_launch, "ops_per_trial": ops_per_trial},
+                         "trials_per_launch": trials_per_launch, "ops_per_trial": ops_per_trial,
+                         "live_candidates_per_trial": live},
         "kernels_ms": {"subsweep_f32": ms_sub, "shift_f32": ms_shift, "draws": ms_draw,
-                       "subsweep_f64": ms_sub64, "shift_f64": ms_shift64},
+                       "subsweep_f32_one_launch": ms_sub_iso, "shift_f32_one_launch": ms_shift_iso,
+                       "subsweep_f64": ms_sub64, "shift_f64": ms_shift64,
+                       "note": "subsweep_f32/shift_f32: mean per launch inside recorded graphs (in-step); "
+                               "*_one_launch and f64: one launch at a time"},
+        "step_check_ms": {"subsweeps_plus_shifts": SWEEPS_PER_STEP * (4 * ms_sub + ms_shift),
+                          "ms_per_step": ms_max / args.steps},
         "fp64": {"value": value64, "unit": "trial moves/s", "ms_per_step": ms64 / max(1, args.fp64_steps),
                  "steps": args.fp64_steps},
         "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
@@ -579,8 +619,8 @@ def run_reference(args):
     nt = oracle.set_threads(os.cpu_count() or 1)
     s = oracle.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, oracle.FP32)
 
-    def step():
-        s.sweep(1)
+    def step():   # the GPU arm's step: 100 sweeps + one contact histogram + the fit
+        s.sweep(SWEEPS_PER_STEP)
         h = s.histogram()
         oracle.pressure.pressure(h, 1, w.N, w.Lx * w.Ly)
 
@@ -608,9 +648,10 @@ def run_reference(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "phi": 0.716, "d": w.d, "nselect": w.nselect,
-                   "step": "1 sweep + contact histogram + pressure fit (CPU oracle)"},
+                   "step": "%d sweeps + contact histogram + pressure fit (CPU oracle)" % SWEEPS_PER_STEP},
         "cpu_baseline": {"value": value, "unit": "trial moves/s", "cores": nt, "kind": "oracle",
-                         "sample": "%d steps of 1 sweep + contact histogram + pressure fit, N=1048576" % args.steps},
+                         "sample": "%d steps of %d sweeps + contact histogram + pressure fit, N=1048576"
+                                   % (args.steps, SWEEPS_PER_STEP)},
         "e2e": {"value": value, "unit": "trial moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

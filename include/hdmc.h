@@ -240,6 +240,18 @@ int hdmc_sync(hdmc_t *h);
  * draws launch (each nullable).  Synchronises. */
 int hdmc_profile_sweeps(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift, double *ms_draws);
 
+/* In-step timing: records n sweeps as CUDA graphs of one stage each, as
+ * hdmc_sweep records them (programmatic dependent launches), and times
+ * their replay with CUDA events on the handle's stream: first the draws and
+ * the four sub-sweeps of each sweep without the shifts, then the draws and
+ * the shifts alone.  Returns the mean milliseconds per sub-sweep launch and
+ * per shift launch inside such a run (each nullable; the draws launch, one
+ * per 64 sweeps, is included).  The configuration stays legal, but the
+ * trajectory is not that of hdmc_sweep (2n sweep indices are used, sub-sweeps
+ * without shifts and shifts without sub-sweeps).  n >= 1, else HDMC_EINVAL.
+ * Synchronises. */
+int hdmc_profile_stages(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift);
+
 /* ---- batched replicas ----------------------------------------------------
  * R independent systems advanced together: every stage of a sweep is one
  * launch over all replicas, recorded into CUDA graphs, so small systems share

@@ -60,6 +60,11 @@ def lib():
             "orc_set_move_size": (ctypes.c_int, [vp, ctypes.c_double]),
             "orc_set_balance": (None, [vp, ctypes.c_int, ctypes.c_int]),
             "orc_set_allow_leave": (ctypes.c_int, [vp, ctypes.c_int]),
+            "orc_set_strips": (ctypes.c_int, [vp, ctypes.c_int]),
+            "orc_sweep_phase": (ctypes.c_int, [vp, ctypes.c_int]),
+            "orc_strip_start": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "orc_get_row": (None, [vp, ctypes.c_int, _f64p, _u8p]),
+            "orc_set_row": (None, [vp, ctypes.c_int, _f64p, _u8p]),
             "orc_sweep_draws": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                        _i32p, _i32p, _f64p]),
             "orc_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
@@ -325,6 +330,35 @@ class System:
         moves that leave the cell are made instead of rejected."""
         if lib().orc_set_allow_leave(self._h, int(allow)):
             raise ValueError("allow_leave failed")
+
+    def set_strips(self, nstrips):
+        """Spatial decomposition with inactive bands (Sec. 6): the first cell
+        row of each of nstrips strips makes no trial moves (0 = none)."""
+        if lib().orc_set_strips(self._h, int(nstrips)):
+            raise ValueError("need my >= 2 nstrips")
+
+    def strip_rows(self, nstrips):
+        """[(first row, end row) of strip k for k < nstrips]."""
+        r = [lib().orc_strip_start(self.my, nstrips, k) for k in range(nstrips)] + [self.my]
+        return [(r[k], r[k + 1]) for k in range(nstrips)]
+
+    def sweep_phase(self, phase):
+        """Phase 0: the sub-sweeps of the next sweep; phase 1: its grid shift."""
+        err = lib().orc_sweep_phase(self._h, int(phase))
+        if err:
+            raise OracleError(err, "sweep_phase")
+
+    def get_row(self, cy):
+        """Cell row cy: (local[mx, 4, 2], counts[mx])."""
+        loc = np.zeros(self.mx * 8, dtype=np.float64)
+        cnt = np.zeros(self.mx, dtype=np.uint8)
+        lib().orc_get_row(self._h, int(cy), _p(loc, _f64p), _p(cnt, _u8p))
+        return loc.reshape(self.mx, 4, 2), cnt
+
+    def set_row(self, cy, local, counts):
+        loc = np.ascontiguousarray(local, dtype=np.float64).reshape(-1)
+        cnt = np.ascontiguousarray(counts, dtype=np.uint8)
+        lib().orc_set_row(self._h, int(cy), _p(loc, _f64p), _p(cnt, _u8p))
 
     def counters(self):
         out = np.zeros(4, dtype=np.uint64)

@@ -227,6 +227,11 @@ typedef struct oracle {
     /* negative control of Sec. 2.4 item 1 (both modes, serial order): 1 = a
      * trial position outside the cell moves the disk into the neighbouring cell */
     int allow_leave;
+    /* spatial decomposition with inactive bands (Sec. 6): 0 = none; else the
+     * rows form nstrips strips and the first row of each strip makes no
+     * trial moves (band[cy] = 1) */
+    int nstrips;
+    uint8_t *band;
 } oracle_t;
 
 static double prev_double(double w) { return nextafter(w, 0.0); }
@@ -273,7 +278,7 @@ static void slot_get(const oracle_t *o, int64_t c, int j, double *x, double *y)
 void orc_destroy(oracle_t *o)
 {
     if (!o) return;
-    free(o->X); free(o->Y); free(o->Xf); free(o->Yf); free(o->n);
+    free(o->X); free(o->Y); free(o->Xf); free(o->Yf); free(o->n); free(o->band);
     free(o);
 }
 
@@ -486,6 +491,68 @@ void orc_set_balance(oracle_t *o, int shuffle_particles, int shuffle_sets)
 {
     o->shuffle_particles = shuffle_particles;
     o->shuffle_sets = shuffle_sets;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial decomposition with inactive bands (Sec. 6).  Several processors    */
+/* would each own a strip of cell rows; if every cell next to another        */
+/* processor's strip made moves, neighbouring processors would have to       */
+/* exchange cells after every sub-sweep.  Instead the first row of every     */
+/* strip is inactive during the sweep's sub-sweeps: no cell of one strip     */
+/* then moves a disk next to a cell another strip moves, and strips need     */
+/* each other's rows only around the grid shift.  Which cells are inactive  */
+/* is fixed in the cell grid, and the grid shift moves the grid relative to */
+/* the disks, so no disk stays frozen.  Strip k (0 <= k < R) is the rows     */
+/* [r_k, r_{k+1}), r_k = 2 floor(k my / (2R)) (even, so every strip starts   */
+/* on the same checkerboard parity; each strip has at least two rows).       */
+/* ------------------------------------------------------------------------ */
+int orc_strip_start(int my, int nstrips, int k)
+{
+    return 2 * (int)(((int64_t)k * my) / (2 * (int64_t)nstrips));
+}
+
+int orc_set_strips(oracle_t *o, int nstrips)
+{
+    if (nstrips < 0 || (nstrips > 0 && o->my < 2 * nstrips)) return ORC_EINVAL;
+    free(o->band);
+    o->band = NULL;
+    o->nstrips = nstrips;
+    if (nstrips == 0) return ORC_OK;
+    o->band = (uint8_t *)calloc((size_t)o->my, 1);
+    if (!o->band) { o->nstrips = 0; return ORC_ENOMEM; }
+    for (int k = 0; k < nstrips; ++k) o->band[orc_strip_start(o->my, nstrips, k)] = 1;
+    return ORC_OK;
+}
+
+/* One cell row in canonical slot order: local[(4 cx + j) 2 + {0,1}], counts[cx]
+ * (unused slots read EMPTY_SLOT).  set_row replaces the row (used to hand
+ * rows between the strips of a decomposed run). */
+void orc_get_row(const oracle_t *o, int cy, double *local, uint8_t *counts)
+{
+    for (int cx = 0; cx < o->mx; ++cx) {
+        int64_t c = (int64_t)cy * o->mx + cx;
+        counts[cx] = o->n[c];
+        for (int j = 0; j < 4; ++j) {
+            double x = EMPTY_SLOT, y = EMPTY_SLOT;
+            if (is_set(o, c, j)) slot_get(o, c, j, &x, &y);
+            local[2 * (4 * cx + j)] = x;
+            local[2 * (4 * cx + j) + 1] = y;
+        }
+    }
+}
+
+void orc_set_row(oracle_t *o, int cy, const double *local, const uint8_t *counts)
+{
+    for (int cx = 0; cx < o->mx; ++cx) {
+        int64_t c = (int64_t)cy * o->mx + cx;
+        o->n[c] = counts[cx];
+        for (int j = 0; j < 4; ++j) {
+            double x = j < counts[cx] ? local[2 * (4 * cx + j)] : EMPTY_SLOT;
+            double y = j < counts[cx] ? local[2 * (4 * cx + j) + 1] : EMPTY_SLOT;
+            if (o->prec == 0) { o->X[4 * c + j] = x; o->Y[4 * c + j] = y; }
+            else { o->Xf[4 * c + j] = (float)x; o->Yf[4 * c + j] = (float)y; }
+        }
+    }
 }
 
 int orc_set_allow_leave(oracle_t *o, int allow)
@@ -929,10 +996,11 @@ static void subsweep(oracle_t *o, uint32_t sweep, int Q)
     int qx = Q & 1, qy = Q >> 1;
     uint64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3) if (!o->allow_leave)
+#pragma omp parallel for schedule(static) reduction(+ : t0, t1, t2, t3) if (!o->allow_leave && o->C >= 4096)
 #endif
     for (int cy = qy; cy < o->my; cy += 2) {
         uint64_t acc[4] = {0, 0, 0, 0};
+        if (o->band && o->band[cy]) continue;   /* inactive band row (Sec. 6) */
         for (int cx = qx; cx < o->mx; cx += 2) {
             if (o->prec == 0) cell_update64(o, sweep, Q, cx, cy, acc);
             else cell_update32(o, sweep, Q, cx, cy, acc);
@@ -1074,6 +1142,23 @@ int orc_sweep(oracle_t *o, int64_t nsweeps)
         if (err != ORC_OK) return err;
     }
     return ORC_OK;
+}
+
+/* One sweep in two phases, as a decomposed run performs it (Sec. 6): phase 0
+ * the four sub-sweeps of sweep o->sweep, phase 1 its grid shift (then the
+ * sweep counter advances).  Phase 0 then phase 1 equals orc_sweep(o, 1). */
+int orc_sweep_phase(oracle_t *o, int phase)
+{
+    uint32_t sweep = (uint32_t)o->sweep;
+    draws_t r;
+    sweep_draws(o->seed, sweep, o->wx, o->wy, &r);
+    if (phase == 0) {
+        for (int q = 0; q < 4; ++q) subsweep(o, sweep, o->shuffle_sets ? r.perm[q] : q);
+        return ORC_OK;
+    }
+    int err = shift_cells(o, r.fdir, r.ds);
+    o->sweep += 1;
+    return err;
 }
 
 /* One explicit extra shift drawn from its own stream (index = #shifts so far). */

@@ -361,6 +361,79 @@ int hdmc_profile_sweeps(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_sh
     return check_device(h);
 }
 
+// stage 1: draws + the four sub-sweeps of each sweep, no shift (the cells stay
+// in one buffer); stage 2: draws + the shift of each sweep.  Programmatic
+// dependent launches as in enqueue_sweeps.
+void enqueue_stage(hdmc_t* h, cudaStream_t s, int K, int parity, int stage) {
+    LaunchCtx c = h->ctx(s);
+    launch_draws(c, h->table, K, true);
+    for (int j = 0; j < K; ++j) {
+        if (stage == 1) {
+            void* a = h->cells[parity];
+            for (int k = 0; k < 4; ++k) {
+                c.pdl = j > 0 || k > 0;
+                if (h->prec == HDMC_FP64) launch_subsweep_f64(c, a, h->table + j, k);
+                else launch_subsweep_f32(c, a, h->table + j, k);
+            }
+        } else {
+            void* a = h->cells[parity ^ (j & 1)];
+            void* b = h->cells[parity ^ (j & 1) ^ 1];
+            c.pdl = j > 0;
+            if (h->prec == HDMC_FP64) launch_shift_f64(c, a, b, h->table + j);
+            else launch_shift_f32(c, a, b, h->table + j);
+        }
+    }
+}
+
+int hdmc_profile_stages(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_shift) {
+    if (!h || n < 1) return HDMC_EINVAL;
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return HDMC_ECUDA;
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return HDMC_ECUDA;
+    }
+    int e = cuda_code(cudaStreamSynchronize(h->stream));
+    double per[3] = {0.0, 0.0, 0.0};
+    for (int stage = 1; stage <= 2 && !e; ++stage) {
+        const int K = (int)std::min<int64_t>(n, kChunk);
+        const int64_t reps = (n + K - 1) / K;
+        // one recorded graph per parity of the state buffer
+        cudaGraphExec_t exec[2] = {nullptr, nullptr};
+        for (int par = 0; par < 2 && !e; ++par) {
+            if (stage == 1 && par == 1) break;
+            cudaGraph_t graph = nullptr;
+            e = cuda_code(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            if (e) break;
+            enqueue_stage(h, h->cap, K, stage == 1 ? h->cur : (h->cur ^ par), stage);
+            e = cuda_code(cudaStreamEndCapture(h->cap, &graph));
+            if (!e) e = cuda_code(cudaGraphInstantiate(&exec[par], graph, 0));
+            if (graph) cudaGraphDestroy(graph);
+        }
+        float ms = 0.f;
+        if (!e) e = cuda_code(cudaEventRecord(ev[0], h->stream));
+        int par = 0;
+        for (int64_t r = 0; r < reps && !e; ++r) {
+            e = cuda_code(cudaGraphLaunch(exec[stage == 1 ? 0 : par], h->stream));
+            h->sweeps += (uint64_t)K;
+            if (stage == 2) par ^= K & 1;
+        }
+        if (!e) e = cuda_code(cudaEventRecord(ev[1], h->stream));
+        if (!e) e = cuda_code(cudaEventSynchronize(ev[1]));
+        if (!e) e = cuda_code(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        if (stage == 2) h->cur ^= par;
+        for (int q = 0; q < 2; ++q)
+            if (exec[q]) cudaGraphExecDestroy(exec[q]);
+        per[stage] = (double)ms / (double)(reps * K * (stage == 1 ? 4 : 1));
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e) return e;
+    if (ms_subsweep) *ms_subsweep = per[1];
+    if (ms_shift) *ms_shift = per[2];
+    return check_device(h);
+}
+
 int hdmc_shift(hdmc_t* h) {
     if (!h) return HDMC_EINVAL;
     const LaunchCtx c = h->ctx(h->stream);

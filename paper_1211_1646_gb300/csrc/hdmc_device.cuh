@@ -34,8 +34,8 @@ constexpr int kFitDegree = 5;             // polynomial degree (Sec. 4)
 
 constexpr uint32_t kDomShuffle = 0u, kDomTrial = 1u, kDomSweep = 2u, kDomInit = 3u, kDomShift = 4u;
 
-constexpr int kShiftBX = 64, kShiftBY = 4;   // shift block: 64 set columns x 4 set rows of one set
 constexpr int kHistBX = 32, kHistBY = 8;     // histogram block: 32 set columns x 8 set rows of one set
+constexpr int kShiftBX = 64, kShiftBY = 4;   // shift block: 64 set columns x 4 set rows of one set
 
 // Geometry and move parameters, passed by value to every kernel.
 struct Geometry {
@@ -87,7 +87,8 @@ struct alignas(16) SweepDraw {
     uint8_t perm[4];       // checkerboard set of sub-sweep k
     float dsf;             // binary32 rounding of ds
     double ds;             // shift distance, uniform in [0, w/2) along f's axis
-    uint32_t pad[2];
+    float dsf2;            // binary32 rounding of ds - dsf (ds = dsf + dsf2 within 2^-48 ds)
+    uint32_t pad[3];
 };
 
 // Device-resident bookkeeping, advanced by the kernels themselves so that a
@@ -208,7 +209,8 @@ __host__ __device__ inline SweepDraw make_draw(const Geometry& g, uint32_t index
     r.dsf = (float)r.ds;
     r.sweep = index;
     for (int q = 0; q < 4; ++q) r.perm[q] = (uint8_t)p[q];
-    r.pad[0] = r.pad[1] = 0;
+    r.dsf2 = (float)(r.ds - (double)r.dsf);
+    r.pad[0] = r.pad[1] = r.pad[2] = 0;
     return r;
 }
 

@@ -12,18 +12,125 @@
 namespace hdmc {
 
 // ---- cell shift: Alg. 4 ----------------------------------------------------------------
+// Every disk is translated by -f*ds (equivalently the grid moves by +f*ds).
 // One thread per new cell; grid (set row, set column, set).  New cell c = the
-// disks of old c that stay inside c after the translation by -f*ds (old slot
-// order), then the disks of old c+f that leave c+f, re-expressed in c's frame
-// (+f*w).  The ownership test is the same expression in the two threads that
-// see a disk, so every disk lands in exactly one cell (Sec. 3.2).  A
-// re-expressed value that rounds onto the upper edge is clamped below it.
-// Grid origin O += f*ds (one thread per shift).  Kept out of line so that the
-// widening to binary64, slow on GB300, stays in that one thread.
-template <typename T>
-__device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax, T sd) {
-    st->origin[ax] += (double)sd;
+// disks of old c that stay inside c (old slot order), then the disks of old
+// c+f that leave c+f, re-expressed in c's frame (+f*w).  The ownership test
+// is the same computation in the two threads that see a disk, so every disk
+// lands in exactly one cell (Sec. 3.2).  A re-expressed value that rounds
+// onto the upper edge is clamped below it.
+//
+// Grid origin O += f*ds (one thread per shift), binary64.  Kept out of line
+// so that the binary64 addition stays in that one thread.
+static __device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax, double sd) {
+    st->origin[ax] = __dadd_rn(st->origin[ax], sd);
 }
+
+// Per-launch constants of the moving coordinate and the evaluation of one
+// disk: whether it stays in its cell, and its new coordinate (in its old
+// cell's frame if it stays, else in the frame of the cell it moves to).
+template <typename T> struct ShiftParams;
+
+// binary64 path: dp = x - sgn ds; stays iff 0 <= dp < w; a migrant's new
+// coordinate dp + sgn w, clamped into [0, w).
+template <> struct ShiftParams<double> {
+    double sd, w, sw, wprev;
+    __device__ ShiftParams(const Geometry& g, const SweepDraw& r, int ax, int sgn) {
+        w = ax ? g.wy : g.wx;
+        sd = sgn > 0 ? r.ds : -r.ds;
+        sw = sgn > 0 ? w : -w;
+        wprev = Prm<double>::prev(w);
+    }
+    __device__ __forceinline__ double origin_step() const { return sd; }
+    __device__ __forceinline__ void disk(double x, bool& stay, double& v) const {
+        const double dp = __dsub_rn(x, sd);
+        stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, w);
+        if (stay) {
+            v = dp;
+        } else {
+            v = __dadd_rn(dp, sw);
+            v = Prm<double>::lt(v, w) ? v : wprev;
+            v = Prm<double>::ge0(v) ? v : 0.0;
+        }
+    }
+};
+
+// binary32 rounding of the real number s + t + eta, |eta| <= mu, |s| >= |t|
+// (s, t binary32): r = RN32(s + t), and s + t = r + rho exactly (Fast2Sum).
+// All reals within mu of s + t round to r when rho stays more than mu inside
+// the rounding interval of r (half an ulp on either side, a quarter ulp below
+// a power of two); otherwise ok is cleared.
+__device__ __forceinline__ float rn32_certified(float s, float t, float mu, bool& ok) {
+    const float r = __fadd_rn(s, t);
+    const float rho = __fsub_rn(t, __fsub_rn(r, s));
+    const uint32_t rb = __float_as_uint(r);
+    const uint32_t e = rb & 0x7F800000u;
+    const float h = __uint_as_float(e - (24u << 23));   // half an ulp of r (exponent field > 24)
+    const float hd = (rb & 0x7FFFFFu) ? h : 0.5f * h;    // below a power of two
+    ok = ok && (rb >> 31) == 0u && e > (24u << 23) &&
+         (rho >= 0.0f ? __fadd_rn(rho, mu) < h : __fsub_rn(mu, rho) < hd);
+    return r;
+}
+
+// binary32 path, remapped in binary64 on the binary32 width W = wf:
+// dp = RN64(x - sgn ds); stays iff 0 <= dp < W; the stored coordinate is
+// RN32(dp) for a stayer and RN32(RN64(dp + sgn W)) for a migrant, clamped
+// below wf.  binary64 arithmetic is slow on this GPU, so the result is
+// computed in binary32 without rounding error where that is possible and
+// certified: sgn ds = d1 + d2 + d3 (d1 = RN32(sgn ds), d2 = RN32(sgn ds -
+// d1), |d3| <= 2^-48 ds); s = RN32(x - d1) with its exact error e
+// (TwoSum); t = RN32(e - d2); then x - sgn ds = s + t + eta with
+// |eta| <= 2^-46 W.  Where s is farther than 2^-20 W from 0 and from W the
+// ownership is decided by s, and rn32_certified rounds the stayer's s + t,
+// the +f migrant's (s + W) + t (Fast2Sum, exact) or the -f migrant's
+// (s - W) + t (s - W exact, Sterbenz) with the bound mu = 2^-43 W on eta,
+// the binary32 rounding of the tails and the binary64 roundings of the
+// remap.  The rest, about one disk in 10^5, is evaluated with binary64
+// instructions.
+template <> struct ShiftParams<float> {
+    float d1, d2, wf, wprev, tau, mu;
+    bool fast;   // the bounds need cell widths far above the binary32 underflow range
+    double sd, W, sW;
+    __device__ ShiftParams(const Geometry& g, const SweepDraw& r, int ax, int sgn) {
+        wf = ax ? g.wyf : g.wxf;
+        wprev = Prm<float>::prev(wf);
+        d1 = sgn > 0 ? r.dsf : -r.dsf;
+        d2 = sgn > 0 ? r.dsf2 : -r.dsf2;
+        tau = __fmul_rn(wf, 0x1p-20f);
+        mu = __fmul_rn(wf, 0x1p-43f);
+        fast = wf > 0x1p-60f;
+        W = (double)wf;
+        sd = sgn > 0 ? r.ds : -r.ds;
+        sW = sgn > 0 ? W : -W;
+    }
+    __device__ __forceinline__ double origin_step() const { return sd; }
+    __device__ __forceinline__ void disk(float x, bool& stay, float& v) const {
+        const float s = __fsub_rn(x, d1);
+        const float bb = __fsub_rn(s, x);   // TwoSum(x, -d1): s + e = x - d1 exactly
+        const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-d1, bb));
+        const float t = __fsub_rn(e, d2);
+        const float sw = __fsub_rn(s, wf);
+        bool ok = fast && fabsf(s) > tau && fabsf(sw) > tau;
+        stay = s > 0.0f && sw < 0.0f;
+        if (!stay) {
+            if (s < 0.0f) {   // +f migrant: (s + W) + t
+                const float s2 = __fadd_rn(s, wf);
+                const float e2 = __fsub_rn(s, __fsub_rn(s2, wf));
+                v = rn32_certified(s2, __fadd_rn(e2, t), mu, ok);
+            } else {          // -f migrant: (s - W) + t
+                v = rn32_certified(sw, t, mu, ok);
+            }
+        } else {
+            v = rn32_certified(s, t, mu, ok);
+        }
+        if (!ok) {   // binary64 instructions, exactly as the rule reads
+            const double dp = __dsub_rn((double)x, sd);
+            stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, W);
+            v = __double2float_rn(stay ? dp : __dadd_rn(dp, sW));
+        }
+        v = v < wf ? v : wprev;   // v >= 0, or -0 from a -0 stayer as the binary64 rule gives
+    }
+};
 
 template <typename T>
 __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restrict__ src, T* __restrict__ dst,
@@ -34,10 +141,8 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     const int fdir = draw->fdir;
     const int ax = fdir >> 1;
     const int sgn = (fdir & 1) ? -1 : 1;
-    const T w = ax ? Prm<T>::wy(g) : Prm<T>::wx(g);
-    const T sd = T(sgn) * Prm<T>::ds(*draw);
-    const T sw = T(sgn) * w;
-    if (hx == 0 && hy == 0 && q == 0) add_origin<T>(st, ax, sd);
+    const ShiftParams<T> P(g, *draw, ax, sgn);
+    if (hx == 0 && hy == 0 && q == 0) add_origin(st, ax, P.origin_step());
     if (hx >= g.hx || hy >= g.hy) return;
     const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
     const int ncx = ax ? cx : wrap(cx + sgn, g.mx);
@@ -50,11 +155,13 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     for (int j = 0; j < 4; ++j) r.x[j] = r.y[j] = T(kEmpty);
     int kept = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 4; ++j) {   // stayers of old c (occupied slots form a prefix)
         if (Prm<T>::ge0(o.x[j])) {
-            const T dp = Prm<T>::sub(ax ? o.y[j] : o.x[j], sd);
-            if (Prm<T>::ge0(dp) && Prm<T>::lt(dp, w)) {
-                const T vx = ax ? o.x[j] : dp, vy = ax ? dp : o.y[j];
+            bool stay;
+            T v;
+            P.disk(ax ? o.y[j] : o.x[j], stay, v);
+            if (stay) {
+                const T vx = ax ? o.x[j] : v, vy = ax ? v : o.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     r.x[s] = (kept == s) ? vx : r.x[s];
@@ -65,13 +172,12 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
         }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 4; ++j) {   // migrants of old c + f
         if (Prm<T>::ge0(b.x[j])) {
-            const T dp = Prm<T>::sub(ax ? b.y[j] : b.x[j], sd);
-            if (!(Prm<T>::ge0(dp) && Prm<T>::lt(dp, w))) {
-                T v = Prm<T>::add(dp, sw);
-                v = Prm<T>::lt(v, w) ? v : Prm<T>::prev(w);
-                v = Prm<T>::ge0(v) ? v : T(0);
+            bool stay;
+            T v;
+            P.disk(ax ? b.y[j] : b.x[j], stay, v);
+            if (!stay) {
                 const T vx = ax ? b.x[j] : v, vy = ax ? v : b.y[j];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {

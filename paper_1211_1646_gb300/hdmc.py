@@ -57,6 +57,7 @@ SIGNATURES = {
     "hdmc_set_stream": (ctypes.c_int, [_vp, _vp]),
     "hdmc_sync": (ctypes.c_int, [_vp]),
     "hdmc_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p, _f64p]),
+    "hdmc_profile_stages": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
     "hdmc_histogram_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_double, _u64p, _vp]),
     "hdmc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, _i64p, _f64p, _f64p, ctypes.c_double,
@@ -304,6 +305,13 @@ def hdmc_profile_sweeps(h, n):
     _check(lib().hdmc_profile_sweeps(h, n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "hdmc_profile_sweeps")
     return a.value, b.value, c.value
+
+
+def hdmc_profile_stages(h, n):
+    """Returns mean ms per (sub-sweep, shift) launch inside recorded graphs of n sweeps of one stage each."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hdmc_profile_stages(h, n, ctypes.byref(a), ctypes.byref(b)), "hdmc_profile_stages")
+    return a.value, b.value
 
 
 def hdmc_histogram_noalloc(dev_local, mx, my, wx, wy, sigma, nbins, dr, stream=None):

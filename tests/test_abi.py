@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -103,3 +105,55 @@ def test_header_is_plain_c_and_links(libpath, tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     e, e3, flags = map(int, r.stdout.split())
     assert e != 0 and e3 != 0 and flags == 0
+
+
+C_GPU_USER = r"""
+#include <stdio.h>
+#include <inttypes.h>
+#include "hdmc.h"
+int main(void) {
+    hdmc_t *h = NULL;
+    double bp = 0.0, g0 = 0.0;
+    uint64_t hist[HDMC_HIST_BINS];
+    int64_t ns = 0;
+    int e = hdmc_create(&h, 1024, 33.89580, 33.89580, 1.0, 0.15, 4, 1u, HDMC_FP32_LOCAL, NULL, 0, NULL);
+    if (e != HDMC_OK) { printf("create %d\n", e); return 1; }
+    e = hdmc_sweep(h, 10);
+    if (e == HDMC_OK) e = hdmc_pressure(h, &bp, &g0, hist, &ns);
+    hdmc_destroy(h);
+    if (e != HDMC_OK) { printf("error %d\n", e); return 2; }
+    printf("%.17g %.17g %" PRId64, bp, g0, ns);
+    for (int i = 0; i < HDMC_HIST_BINS; ++i) printf(" %" PRIu64, hist[i]);
+    printf("\n");
+    return 0;
+}
+"""
+
+
+@pytest.mark.gpu
+def test_c_caller_on_gpu_matches_oracle(libpath, tmp_path):
+    # A plain C99 program drives the library through the C ABI alone (create,
+    # 10 binary32 sweeps, pressure): its contact histogram is bit-identical to
+    # the oracle's after the same sweeps, and its pressure is the Sec. 4 fit.
+    import subprocess
+    import oracle as O
+    from oracle import pressure as P
+    src = tmp_path / "gpu_user.c"
+    src.write_text(C_GPU_USER)
+    exe = tmp_path / "gpu_user"
+    libdir = os.path.dirname(libpath)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lhdmc",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    f = r.stdout.split()
+    bp, ns = float(f[0]), int(f[2])
+    hist = np.array([int(x) for x in f[3:]], dtype=np.uint64)
+    ref = O.System(1024, 33.89580, 33.89580, 1.0, 0.15, 4, 1, O.FP32)
+    ref.sweep(10)
+    href = ref.histogram(200, 1e-4)
+    assert ns == 1 and hist.sum() > 0 and np.array_equal(hist, href)
+    bp_ref = P.pressure(href, 1, 1024, 33.89580 * 33.89580)[0]
+    assert abs(bp - bp_ref) < 1e-9 * abs(bp_ref), (bp, bp_ref)
+

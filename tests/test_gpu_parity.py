@@ -186,6 +186,57 @@ def test_explicit_shift(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_many_explicit_shifts(prec):
+    # 3000 shifts of a 1024-disk system: every shift direction and distance,
+    # including the rare distances below 2^-9 that the binary32 path's shift
+    # remaps with binary64 instructions instead of fixed point (Alg. 4).
+    w = W.n1024_phi070()
+    g, r = _pair(w, prec)
+    g.sweep(3)
+    r.sweep(3)
+    for k in range(6):
+        for _ in range(500):
+            g.shift()
+            r.shift()
+        _same(g, r, "after %d shifts" % (500 * (k + 1)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shift_edge_cases(prec):
+    # Disks exactly on and one ulp inside cell edges (the ownership test of
+    # Sec. 3.2 decides them), and disks with tiny local coordinates (binary32
+    # values below the fixed-point range of the binary32 shift, and a
+    # subnormal one), through 400 shifts and a few sweeps, bit for bit.
+    from paper_1211_1646_gb300 import hdmc
+    L = 17.0
+    mx, my, wx, wy = O.grid(L, L)
+    pts = []
+    for cy in range(0, my, 2):
+        for cx in range(2, mx, 2):
+            base = np.array([cx * wx, cy * wy])
+            for off in ([0.0, 0.0], [np.nextafter(wx, 0), np.nextafter(wy, 0)]):
+                pts.append(base + off)
+    tiny = [1e-30, 1e-40, 2.0**-37, 2.0**-36, 3e-12, 1e-20, 2.0**-38 + 2.0**-60, 5e-45]
+    for k, v in enumerate(tiny):
+        pts.append([v, (2 * k + 1) * wy])
+        pts.append([2 * wx, (2 * k + 1) * wy + v])
+    xy = np.array(pts)
+    assert len(xy) == 128   # the library's lattice start (replaced by xy) must be legal for this N
+    xy = np.where(xy >= L, xy - L, xy)
+    g = hdmc.System(len(xy), L, L, 1.0, 0.1, 4, 5, prec, xy=xy)
+    r = O.System(len(xy), L, L, 1.0, 0.1, 4, 5, PREC[prec], xy=xy)
+    _same(g, r, "start")
+    for k in range(8):
+        for _ in range(50):
+            g.shift()
+            r.shift()
+        _same(g, r, "after %d shifts" % (50 * (k + 1)))
+    g.sweep(20)
+    r.sweep(20)
+    _same(g, r, "after sweeps")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_contact_histogram_and_pressure(prec):
     w = W.n65536_phi070()
     g, r = _pair(w, prec)

@@ -231,14 +231,19 @@ def _min_image(d, L):
 R_MIN = {O.FP64: 1.0 - 1e-12, O.FP32: 1.0 - 1e-6}
 
 
+@pytest.mark.parametrize("strips", [0, 2])
 @pytest.mark.parametrize("prec", [O.FP64, O.FP32])
-def test_two_disks_sample_the_uniform_distribution(prec):
+def test_two_disks_sample_the_uniform_distribution(prec, strips):
     # Detailed balance (Sec. 2.3) makes the uniform measure on legal
     # configurations stationary: the separation of two disks on a 4x4 torus
     # is uniform over the square [-2,2)^2 minus the disk |r| < sigma.  Both
     # arithmetic modes of the oracle must sample it.
     L = 4.0
+    # strips = 2: the spatial decomposition of Sec. 6, rows 0 and 2 of the
+    # 4-row grid make no moves during the sub-sweeps; the grid shift moves
+    # the frozen rows over the disks, and the chain samples the same measure
     s = O.System(2, L, L, 1.0, 0.45, 4, 2024, prec, xy=np.array([[0.5, 0.5], [2.5, 2.5]]))
+    s.set_strips(strips)
     assert s.box() == (L, L)
     s.sweep(200)
     seps = []
@@ -300,8 +305,9 @@ def test_two_disk_pin_detects_moves_that_leave_the_cell(prec):
     assert c[2] == 0 and c[1] > 0.9 * c[0]              # no move is rejected for leaving
 
 
+@pytest.mark.parametrize("strips", [0, 2])
 @pytest.mark.parametrize("prec", [O.FP64, O.FP32])
-def test_tiny_system_matches_rejection_sampling(prec):
+def test_tiny_system_matches_rejection_sampling(prec, strips):
     # 4 disks on a 4.4 x 4.4 torus: pair-distance distribution of the Markov
     # chain equals that of independent uniform legal configurations.  With
     # cells of width 1.1, two disks share a cell often enough that a wrong
@@ -316,6 +322,7 @@ def test_tiny_system_matches_rejection_sampling(prec):
             ref.append(min(ds))
     start = np.array([[0.5, 0.5], [2.7, 0.5], [0.5, 2.7], [2.7, 2.7]])
     s = O.System(4, L, L, 1.0, 0.4, 4, 77, prec, xy=start)
+    s.set_strips(strips)   # 2: inactive bands on rows 0 and 2 (Sec. 6)
     Lx, Ly = s.box()   # binary32 mode: 4 x float(1.1), a hair above 4.4
     s.sweep(200)
     mc = []
@@ -456,3 +463,35 @@ def test_low_density_virial_series(prec):
     assert abs(mean - series) < 3 * se + 1e-3, (mean, se, series)
     # the second-order term alone is resolved
     assert abs(mean - (1 + B2 * rho)) > 3 * se
+
+
+def test_inactive_bands_make_no_moves():
+    # Sec. 6 decomposition: strip k starts at row 2 floor(k my / (2R)); that
+    # row makes no trial moves during the sub-sweeps, every other cell makes
+    # n_M (trials = n_M x occupied cells off the band rows), and the band
+    # rows' disks still move with the grid shift.
+    w = W.n1024_phi070()
+    for prec in (O.FP64, O.FP32):
+        for R in (1, 3, 16):
+            s = O.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 9, prec)
+            s.set_strips(R)
+            rows = s.strip_rows(R)
+            assert rows[0][0] == 0 and rows[-1][1] == s.my
+            assert all(b - a >= 2 and a % 2 == 0 for a, b in rows)
+            band = [a for a, _ in rows]
+            for sweep in range(3):
+                loc, cnt = s.state()
+                before = [s.get_row(r)[0].copy() for r in band]
+                occ = cnt.reshape(s.my, s.mx)
+                active = int((occ > 0).sum() - sum((occ[r] > 0).sum() for r in band))
+                c0 = s.counters().copy()
+                for Q in range(4):
+                    s.subsweep(sweep, Q)
+                assert int(s.counters()[0] - c0[0]) == 4 * active
+                for r, b in zip(band, before):
+                    assert np.array_equal(s.get_row(r)[0], b)
+            s.sweep(20)
+            assert s.local_overlaps() == 0 and int(s.state()[1].sum()) == w.N
+    with pytest.raises(ValueError):
+        O.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 9, O.FP64).set_strips(17)   # my = 32 < 2 x 17
+
