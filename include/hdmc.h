@@ -62,6 +62,17 @@ extern "C" {
 #define HDMC_FP64 0       /* binary64 cell-local offsets; bit-identical to the serial reference */
 #define HDMC_FP32_LOCAL 1 /* binary32 cell-local offsets (Sec. 5 stores binary32 coordinates) */
 
+/* ---- cell rule, OR-ed into the precision argument of hdmc_create,
+ * hdmc_workspace_bytes, hdmc_strip_create and the batch calls ----
+ * By default m = largest even integer <= L/sigma per axis (cells just wider
+ * than sigma, about 0.9 disks per cell in a dense fluid).  With
+ * HDMC_CELLS_SQRT2, the paper's rule (Sec. 3.1): floor(L/(sqrt(2) sigma))
+ * rounded up to the smallest even m > L/(sqrt(2) sigma), the widest cells
+ * that still hold at most four centres (Fig. 3; about 1.8 disks per cell).
+ * Either way w = L/m with sigma <= w < sqrt(2) sigma; HDMC_EINVAL if the
+ * rule gives fewer than 4 cells or cells narrower than sigma. */
+#define HDMC_CELLS_SQRT2 0x100
+
 #define HDMC_EMPTY_SLOT (-1.0e4)
 #define HDMC_HIST_BINS 200 /* contact histogram: bins of 1e-4 sigma over [sigma, 1.02 sigma) (Sec. 4) */
 
@@ -252,6 +263,85 @@ int hdmc_profile_sweeps(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_sh
  * Synchronises. */
 int hdmc_profile_stages(hdmc_t *h, int64_t n, double *ms_subsweep, double *ms_shift);
 
+/* ---- spatial decomposition with inactive bands (Sec. 6) -------------------
+ * A system split across processors by strips of cell rows.  Strip k of R
+ * owns the global rows [r_k, r_{k+1}), r_k = 2 floor(k my / (2R)) (even;
+ * every strip has at least two rows, so my >= 2R).  The strip's first row is
+ * an inactive band: its cells make no trial moves during the sub-sweeps, so
+ * no cell of one strip moves a disk next to a cell another strip moves, and
+ * neighbouring strips exchange rows only around the grid shift, which moves
+ * the grid (and so the bands) over the disks (Sec. 6 proposes exactly this
+ * to cut the communication between processors to once per sweep).  The same
+ * chain, serially, is the whole system with those rows inactive.
+ *
+ * A strip handle holds its rows and two halo rows on either side (rows
+ * r_k - 2, r_k - 1 below and r_{k+1}, r_{k+1} + 1 above, periodic) and
+ * sweeps in two phases; per sweep, every strip:
+ *   1. hdmc_strip_subsweeps: the sweep's draws and its four sub-sweeps;
+ *   2. sends its last row (hdmc_strip_get_row which = 3) to the next strip,
+ *      which stores it as its halo row r_k - 1 (hdmc_strip_set_halo
+ *      which = 1): the shift moves disks of that row into the strip;
+ *   3. hdmc_strip_shift: the sweep's grid shift of the strip's own rows;
+ *   4. sends its first row (which = 0, the band) to the previous strip, which
+ *      stores it as its halo row r_{k+1} (which = 2): the neighbours of that
+ *      strip's last row during the next sub-sweeps.
+ * The contact histogram (hdmc_sample, then hdmc_strip_histogram) counts the
+ * pairs of the strip's own disks and needs all four halo rows current: rows
+ * r_k, r_k + 1 (which 0, 1) to the previous strip's halos 2, 3, and rows
+ * r_{k+1} - 2, r_{k+1} - 1 (which 2, 3) to the next strip's halos 0, 1.
+ * The random streams are keyed by global cell numbers, so the strips
+ * together follow the serial chain bit for bit.  Other entry points that
+ * take an hdmc_t accept a strip handle only where noted (hdmc_sample,
+ * hdmc_get_state (local rows, halos included), hdmc_counters (the strip's
+ * own trials), hdmc_info, hdmc_sync, hdmc_set_stream, hdmc_set_move_size,
+ * hdmc_set_balance, hdmc_destroy); the rest return HDMC_EINVAL. */
+
+/* Creates strip `strip` (0 <= strip < nstrips) of the system hdmc_create
+ * would build from the same arguments (hexagonal start), with device memory
+ * from cudaMalloc, freed by hdmc_destroy.  Errors as hdmc_create, and
+ * HDMC_EINVAL for a bad strip or my < 2 nstrips.  Synchronises. */
+int hdmc_strip_create(hdmc_t **out, int64_t N, double Lx, double Ly, double sigma, double d, int nselect,
+                      uint64_t seed, int precision, int32_t nstrips, int32_t strip, void *stream);
+
+/* Global rows [first_row, end_row) the strip owns. */
+int hdmc_strip_rows(hdmc_t *h, int32_t *first_row, int32_t *end_row);
+
+/* Phase 1 of the next sweep: its draws and its four sub-sweeps (the band and
+ * the halo rows make no moves).  Enqueued on the handle's stream.
+ * HDMC_EINVAL if the previous sweep's shift is still missing. */
+int hdmc_strip_subsweeps(hdmc_t *h);
+
+/* Phase 2: the sweep's grid shift of the strip's own rows (Alg. 4); reads
+ * the halo rows r_k - 1 and r_{k+1}.  HDMC_EINVAL without phase 1. */
+int hdmc_strip_shift(hdmc_t *h);
+
+/* Bytes of one cell row in the library's layout (mx cells, 8 coordinates
+ * each: the even-x cells, then the odd-x cells). */
+size_t hdmc_strip_row_bytes(const hdmc_t *h);
+
+/* Copies an own row of the current state into buf (host or device memory,
+ * hdmc_strip_row_bytes long): which = 0, 1, 2, 3 for rows r_k, r_k + 1,
+ * r_{k+1} - 2, r_{k+1} - 1.  Synchronises the handle's stream. */
+int hdmc_strip_get_row(hdmc_t *h, int32_t which, void *buf);
+
+/* Replaces a halo row with buf (as written by hdmc_strip_get_row of the
+ * strip that owns the row): which = 0, 1, 2, 3 for rows r_k - 2, r_k - 1,
+ * r_{k+1}, r_{k+1} + 1.  Synchronises the handle's stream. */
+int hdmc_strip_set_halo(hdmc_t *h, int32_t which, const void *buf);
+
+/* The strip's contact histogram accumulated by hdmc_sample since the last
+ * call (HDMC_HIST_BINS counts, host; ordered pairs with the first disk in
+ * the strip's own rows) and the number of samples; clears it.  Synchronises. */
+int hdmc_strip_histogram(hdmc_t *h, uint64_t *hist, int64_t *n_samples);
+
+/* The Sec. 4 estimator on a histogram of n_samples configurations of N
+ * disks in an Lx x Ly box (for example the sum of the strips' histograms):
+ * g(R_i) (Eqs. gR, R), the degree-5 least-squares fit over (sigma, 1.02
+ * sigma], g(sigma+) and beta P / rho = 1 + (pi/2) rho sigma^2 g(sigma+)
+ * (Eq. P).  Host only. */
+int hdmc_pressure_fit(const uint64_t *hist, int64_t n_samples, int64_t N, double Lx, double Ly, double sigma,
+                      double *betaP_over_rho, double *g_contact);
+
 /* ---- batched replicas ----------------------------------------------------
  * R independent systems advanced together: every stage of a sweep is one
  * launch over all replicas, recorded into CUDA graphs, so small systems share
@@ -289,6 +379,15 @@ int hdmc_batch_pressure(hdmc_batch_t *b, double *betaP_over_rho, double *g_conta
 
 /* Raw state of replica r in the layout of hdmc_get_state.  Synchronises. */
 int hdmc_batch_get_state(hdmc_batch_t *b, int r, double *local, uint8_t *counts);
+
+/* Replaces replica r's configuration, grid origin and sweep counter, as
+ * hdmc_set_state does for a single system (same layout, same checks:
+ * HDMC_EINVAL for a count above 4, a coordinate outside its cell or not a
+ * binary32 value in a binary32 batch, or a disk total other than the
+ * replica's N; nothing changes then).  The other replicas are untouched.
+ * Synchronises. */
+int hdmc_batch_set_state(hdmc_batch_t *b, int r, const double *local, const uint8_t *counts,
+                         const double origin[2], uint64_t sweeps_done);
 
 /* Batch snapshots, as hdmc_save / hdmc_load for every replica at once: a
  * 256-byte header (magic "HDMCBSN1", version, precision, R, sub-sweep

@@ -47,6 +47,8 @@ def lib():
             "orc_sym52": (ctypes.c_double, [ctypes.c_uint32, ctypes.c_uint32]),
             "orc_grid": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _i32p, _i32p,
                                         _f64p, _f64p]),
+            "orc_grid_rule": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _i32p,
+                                             _i32p, _f64p, _f64p]),
             "orc_lattice_shape": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _i64p, _i64p]),
             "orc_lattice_positions": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_double, ctypes.c_uint64, _f64p]),
@@ -160,10 +162,14 @@ def lemire_exhaustive(rng):
     return out
 
 
-def grid(Lx, Ly, sigma=1.0):
+CELLS_SIGMA, CELLS_SQRT2 = 0, 1   # grid rules: cells just wider than sigma / the paper's just below sqrt(2) sigma
+
+
+def grid(Lx, Ly, sigma=1.0, cells=CELLS_SIGMA):
     mx, my = ctypes.c_int32(), ctypes.c_int32()
     wx, wy = ctypes.c_double(), ctypes.c_double()
-    err = lib().orc_grid(Lx, Ly, sigma, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(wx), ctypes.byref(wy))
+    err = lib().orc_grid_rule(Lx, Ly, sigma, cells, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(wx),
+                              ctypes.byref(wy))
     if err:
         raise ValueError("invalid box")
     return mx.value, my.value, wx.value, wy.value
@@ -271,14 +277,15 @@ class OracleError(RuntimeError):
 class System:
     """One hard-disk system advanced by the oracle."""
 
-    def __init__(self, N, Lx, Ly, sigma=1.0, d=0.1, nselect=4, seed=1, precision=FP64, xy=None):
+    def __init__(self, N, Lx, Ly, sigma=1.0, d=0.1, nselect=4, seed=1, precision=FP64, xy=None, cells=CELLS_SIGMA):
         self._h = ctypes.c_void_p()
         L = lib()
+        mode = precision + 256 * cells
         if xy is None:
-            err = L.orc_create(ctypes.byref(self._h), N, Lx, Ly, sigma, d, nselect, seed, precision)
+            err = L.orc_create(ctypes.byref(self._h), N, Lx, Ly, sigma, d, nselect, seed, mode)
         else:
             xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
-            err = L.orc_create_from(ctypes.byref(self._h), N, Lx, Ly, sigma, d, nselect, seed, precision,
+            err = L.orc_create_from(ctypes.byref(self._h), N, Lx, Ly, sigma, d, nselect, seed, mode,
                                     _p(xy, _f64p))
         if err:
             raise OracleError(err, "create")

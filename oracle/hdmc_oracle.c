@@ -245,19 +245,36 @@ static int overlap32(float dx, float dy, float sig2)
     return fmaf(dx, dx, fmaf(dy, dy, -sig2)) < 0.0f;
 }
 
-/* Grid rule: mx = largest even integer <= Lx/sigma, likewise my. */
-static int grid_size(double L, double sigma)
+/* Grid rules (both give an even m, which the checkerboard of Eq. 1 needs on a
+ * periodic box, and sigma <= w < sqrt(2) sigma, so a cell holds at most four
+ * centres, Fig. 3):
+ *   0: m = largest even integer <= L/sigma (cells just wider than sigma);
+ *   1: the paper's rule of Sec. 3.1, m = floor(L/(sqrt(2) sigma)) rounded up:
+ *      the smallest even m > L/(sqrt(2) sigma), the widest cells that still
+ *      hold at most four centres. */
+#define CELLS_SQRT2 1
+static int grid_size_rule(double L, double sigma, int rule)
 {
     double q = floor(L / sigma);
     if (q > 2.0e9) return -1;
     int m = (int)q;
-    return m - (m & 1);
+    m -= m & 1;
+    if (rule == CELLS_SQRT2) {
+        double r = floor(L / (sqrt(2.0) * sigma)) + 1.0;
+        int k = (int)r;
+        k += k & 1;
+        if (k > m) return -1;   /* w would fall below sigma */
+        m = k;
+    }
+    return m;
 }
 
-int orc_grid(double Lx, double Ly, double sigma, int32_t *mx, int32_t *my, double *wx, double *wy)
+static int grid_size(double L, double sigma) { return grid_size_rule(L, sigma, 0); }
+
+int orc_grid_rule(double Lx, double Ly, double sigma, int rule, int32_t *mx, int32_t *my, double *wx, double *wy)
 {
-    if (!(sigma > 0) || !(Lx > 0) || !(Ly > 0)) return ORC_EINVAL;
-    int a = grid_size(Lx, sigma), b = grid_size(Ly, sigma);
+    if (!(sigma > 0) || !(Lx > 0) || !(Ly > 0) || rule < 0 || rule > 1) return ORC_EINVAL;
+    int a = grid_size_rule(Lx, sigma, rule), b = grid_size_rule(Ly, sigma, rule);
     if (a < 4 || b < 4) return ORC_EINVAL;
     *mx = a; *my = b;
     *wx = Lx / a; *wy = Ly / b;
@@ -265,6 +282,11 @@ int orc_grid(double Lx, double Ly, double sigma, int32_t *mx, int32_t *my, doubl
     if (!((*wx) * (*wx) < 2.0 * sigma * sigma) || !((*wy) * (*wy) < 2.0 * sigma * sigma))
         return ORC_EINVAL;
     return ORC_OK;
+}
+
+int orc_grid(double Lx, double Ly, double sigma, int32_t *mx, int32_t *my, double *wx, double *wy)
+{
+    return orc_grid_rule(Lx, Ly, sigma, 0, mx, my, wx, wy);
 }
 
 static int is_set(const oracle_t *o, int64_t c, int j) { return j < o->n[c]; }
@@ -288,8 +310,11 @@ static oracle_t *alloc_state(int64_t N, double Lx, double Ly, double sigma, doub
     int32_t mx, my;
     double wx, wy;
     *err = ORC_EINVAL;
+    /* prec: arithmetic mode (bits 0-7), optionally + 256 * grid rule */
+    int rule = prec >> 8;
+    prec &= 0xFF;
     if (N < 1 || nsel < 1 || nsel > 255 || (prec != 0 && prec != 1)) return NULL;
-    if (orc_grid(Lx, Ly, sigma, &mx, &my, &wx, &wy) != ORC_OK) return NULL;
+    if (orc_grid_rule(Lx, Ly, sigma, rule, &mx, &my, &wx, &wy) != ORC_OK) return NULL;
     if (!(d > 0) || !(d < 0.5 * wx) || !(d < 0.5 * wy)) return NULL;
     if ((int64_t)mx * my * NMAX < N) return NULL;
     oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));

@@ -76,6 +76,11 @@ struct hdmc_handle {
     uint64_t sweeps = 0, shifts = 0;
     int64_t n_samples = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (sweeps, parity) -> graph
+    // strip of a decomposed system (Sec. 6); nstrips == 0 for a whole system
+    int nstrips = 0, strip = 0;
+    int r0 = 0, r1 = 0;       // global rows [r0, r1) owned by the strip
+    int myg = 0;              // rows of the whole grid
+    bool pending = false;     // sub-sweeps of a sweep done, its shift not yet
 
     LaunchCtx ctx(cudaStream_t s) const {
         LaunchCtx c;
@@ -186,8 +191,10 @@ extern "C" {
 size_t hdmc_workspace_bytes(int64_t N, double Lx, double Ly, double sigma, int precision) {
     int mx, my;
     double wx, wy;
+    const int rule = precision >> 8;
+    precision &= 0xFF;
     if (N < 1 || (precision != HDMC_FP64 && precision != HDMC_FP32_LOCAL)) return 0;
-    if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy)) return 0;
+    if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy, rule)) return 0;
     if ((int64_t)mx * my >= (int64_t(1) << 32)) return 0;   // as hdmc_create
     Geometry g{};
     g.mx = mx;
@@ -215,10 +222,10 @@ int hdmc_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, dou
     h->N = N;
     h->Lx = Lx;
     h->Ly = Ly;
-    h->prec = precision;
+    h->prec = desc.prec;
     const Geometry& g = h->g;
     h->stream = (cudaStream_t)stream;
-    h->lay = make_layout(g, precision);
+    h->lay = make_layout(g, desc.prec);
 
     int e = HDMC_OK;
     if (dev_workspace) {
@@ -275,6 +282,7 @@ int hdmc_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, dou
 
 int hdmc_set_positions(hdmc_t* h, const double* xy) {
     if (!h || !xy) return HDMC_EINVAL;
+    if (h && h->nstrips) return HDMC_EINVAL;
     HostState hs;
     int e = bin_positions(h->desc(), xy, hs);
     if (e) return e;
@@ -295,6 +303,7 @@ int hdmc_set_positions(hdmc_t* h, const double* xy) {
 
 int hdmc_sweep(hdmc_t* h, int64_t n) {
     if (!h || n < 0) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     while (n > 0) {
         const int K = (int)std::min<int64_t>(n, kChunk);
         cudaGraphExec_t exec;
@@ -311,6 +320,7 @@ int hdmc_sweep(hdmc_t* h, int64_t n) {
 
 int hdmc_profile_sweeps(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_shift, double* ms_draws) {
     if (!h || n < 0) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     const int nev = 2;
     cudaEvent_t ev[nev];
     for (int i = 0; i < nev; ++i)
@@ -387,6 +397,7 @@ void enqueue_stage(hdmc_t* h, cudaStream_t s, int K, int parity, int stage) {
 
 int hdmc_profile_stages(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_shift) {
     if (!h || n < 1) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     cudaEvent_t ev[2];
     if (cudaEventCreate(&ev[0]) != cudaSuccess) return HDMC_ECUDA;
     if (cudaEventCreate(&ev[1]) != cudaSuccess) {
@@ -436,6 +447,7 @@ int hdmc_profile_stages(hdmc_t* h, int64_t n, double* ms_subsweep, double* ms_sh
 
 int hdmc_shift(hdmc_t* h) {
     if (!h) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     const LaunchCtx c = h->ctx(h->stream);
     launch_draws(c, h->shift_table, 1, false);
     if (h->prec == HDMC_FP64) launch_shift_f64(c, h->cells[h->cur], h->cells[h->cur ^ 1], h->shift_table);
@@ -456,6 +468,7 @@ int hdmc_sample(hdmc_t* h) {
 
 int hdmc_pressure(hdmc_t* h, double* betaP_over_rho, double* g_contact, uint64_t* hist, int64_t* n_samples) {
     if (!h) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // a strip's histogram: hdmc_strip_histogram
     int e = HDMC_OK;
     if (h->n_samples == 0) e = hdmc_sample(h);
     if (!e) e = check_device(h);
@@ -478,6 +491,7 @@ int hdmc_pressure(hdmc_t* h, double* betaP_over_rho, double* g_contact, uint64_t
 
 int hdmc_psi6(hdmc_t* h, double r_cut, double out[4], double* psi) {
     if (!h || !out) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     const double wmin = h->prec == HDMC_FP64 ? std::min(h->g.wx, h->g.wy)
                                              : std::min((double)h->g.wxf, (double)h->g.wyf);
     if (!(r_cut > 0.0) || !(r_cut <= 2.0 * wmin)) return HDMC_EINVAL;
@@ -511,6 +525,7 @@ int hdmc_psi6(hdmc_t* h, double r_cut, double out[4], double* psi) {
 
 int hdmc_positions(hdmc_t* h, double* xy, int32_t* cell) {
     if (!h || !xy) return HDMC_EINVAL;
+    if (h->nstrips) return HDMC_EINVAL;   // strips sweep in two phases (hdmc_strip_*)
     HostState hs;
     int e = download(h, hs);
     DevState ds;
@@ -553,26 +568,11 @@ int hdmc_get_state(hdmc_t* h, double* local, uint8_t* counts) {
 int hdmc_set_state(hdmc_t* h, const double* local, const uint8_t* counts, const double origin[2],
                    uint64_t sweeps_done, uint64_t shifts_done) {
     if (!h || !local || !counts || !origin) return HDMC_EINVAL;
-    const Geometry& g = h->g;
+    if (h && h->nstrips) return HDMC_EINVAL;
     HostState hs;
-    hs.loc.assign(8 * (size_t)g.C, kEmpty);
-    hs.cnt.assign(counts, counts + g.C);
-    int64_t total = 0;
-    for (int64_t c = 0; c < g.C; ++c) {
-        if (hs.cnt[c] > kSlots) return HDMC_EINVAL;
-        total += hs.cnt[c];
-        for (int j = 0; j < hs.cnt[c]; ++j) {
-            const double x = local[2 * (4 * c + j)], y = local[2 * (4 * c + j) + 1];
-            const bool fits = h->prec == HDMC_FP64 ? (x >= 0 && x < g.wx && y >= 0 && y < g.wy)
-                                                   : ((double)(float)x == x && (double)(float)y == y && x >= 0 &&
-                                                      (float)x < g.wxf && y >= 0 && (float)y < g.wyf);
-            if (!fits) return HDMC_EINVAL;
-            hs.loc[2 * (4 * c + j)] = x;
-            hs.loc[2 * (4 * c + j) + 1] = y;
-        }
-    }
-    if (total != h->N) return HDMC_EINVAL;
-    int e = cuda_code(cudaStreamSynchronize(h->stream));
+    int e = state_from_local(h->desc(), local, counts, hs);
+    if (e) return e;
+    e = cuda_code(cudaStreamSynchronize(h->stream));
     if (!e) e = upload(h, hs);
     DevState ds;
     if (!e) e = read_devstate(h, ds);
@@ -633,6 +633,7 @@ SnapLayout snap_layout(const hdmc_t* h) {
 size_t hdmc_snapshot_bytes(const hdmc_t* h) { return h ? snap_layout(h).total : 0; }
 
 int hdmc_save(hdmc_t* h, void* buf, size_t bytes) {
+    if (h && h->nstrips) return HDMC_EINVAL;
     if (!h || !buf) return HDMC_EINVAL;
     const SnapLayout L = snap_layout(h);
     if (bytes < L.total) return HDMC_EINVAL;
@@ -681,6 +682,7 @@ int hdmc_save(hdmc_t* h, void* buf, size_t bytes) {
 }
 
 int hdmc_load(hdmc_t* h, const void* buf, size_t bytes) {
+    if (h && h->nstrips) return HDMC_EINVAL;
     if (!h || !buf) return HDMC_EINVAL;
     const SnapLayout L = snap_layout(h);
     if (bytes < L.total) return HDMC_EINVAL;
@@ -836,6 +838,223 @@ void hdmc_destroy(hdmc_t* h) {
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     delete h;
+}
+
+// ---- spatial decomposition with inactive bands (Sec. 6) ---------------------------
+namespace {
+
+// First row of strip k of R: 2 floor(k my / (2R)) (even, so every strip
+// starts on the same checkerboard parity; every strip has >= 2 rows).
+int strip_start(int my, int R, int k) { return 2 * (int)(((int64_t)k * my) / (2 * (int64_t)R)); }
+
+// Local row of a strip handle holding global row gy: rows r0-2 .. r1+1 are
+// local rows 0 .. my-1 (periodic in the global rows).
+int strip_local_row(const hdmc_t* h, int which) {
+    const int own = h->r1 - h->r0;
+    switch (which) {   // own edge rows r0, r0+1, r1-2, r1-1 / halo rows r0-2, r0-1, r1, r1+1
+        case 0: return 2;
+        case 1: return 3;
+        case 2: return own;
+        case 3: return own + 1;
+        case 4: return 0;
+        case 5: return 1;
+        case 6: return own + 2;
+        case 7: return own + 3;
+        default: return -1;
+    }
+}
+
+// Copies local row ly between the current cell buffer and buf (host or
+// device memory): the row's even-x cells then its odd-x cells, each a
+// contiguous run of mx/2 cells of the set-major layout.
+int strip_copy_row(hdmc_t* h, int ly, void* buf, bool to_buf) {
+    const Geometry& g = h->g;
+    const size_t el = h->prec == HDMC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t half = (size_t)g.hx * 8 * el;
+    char* cells = (char*)h->cells[h->cur];
+    int e = HDMC_OK;
+    for (int p = 0; p < 2 && !e; ++p) {
+        const long long s0 = storage_index(g, p, ly);   // first cell of the half row
+        char* dev = cells + (size_t)s0 * 8 * el;
+        char* b = (char*)buf + p * half;
+        e = cuda_code(to_buf ? cudaMemcpyAsync(b, dev, half, cudaMemcpyDefault, h->stream)
+                             : cudaMemcpyAsync(dev, b, half, cudaMemcpyDefault, h->stream));
+    }
+    if (!e) e = cuda_code(cudaStreamSynchronize(h->stream));
+    return e;
+}
+
+}  // namespace
+
+int hdmc_strip_create(hdmc_t** out, int64_t N, double Lx, double Ly, double sigma, double d, int nselect,
+                      uint64_t seed, int precision, int32_t nstrips, int32_t strip, void* stream) {
+    if (!out) return HDMC_EINVAL;
+    *out = nullptr;
+    if (N < 2 || (N & 1)) return HDMC_EINVAL;
+    SysDesc G;
+    int e = make_system(G, N, Lx, Ly, sigma, d, nselect, seed, precision);
+    if (e) return e;
+    if (nstrips < 1 || strip < 0 || strip >= nstrips || G.g.my < 2 * nstrips) return HDMC_EINVAL;
+    HostState whole;
+    e = start_state(G, whole);
+    if (e) return e;
+    hdmc_t* h = new (std::nothrow) hdmc_t();
+    if (!h) return HDMC_ENOMEM;
+    h->nstrips = nstrips;
+    h->strip = strip;
+    h->myg = G.g.my;
+    h->r0 = strip_start(G.g.my, nstrips, strip);
+    h->r1 = strip + 1 == nstrips ? G.g.my : strip_start(G.g.my, nstrips, strip + 1);
+    const int own = h->r1 - h->r0;
+    Geometry g = G.g;
+    g.my = own + 4;   // two halo rows on either side; even, as own is
+    g.hy = g.my / 2;
+    g.cq = (long long)g.hx * g.hy;
+    g.C = (long long)g.mx * g.my;
+    g.row0 = h->r0 - 2;
+    g.ylo = 3;          // the strip's first row (global r0) is its inactive band
+    g.yhi = own + 1;
+    g.slo = 2;
+    g.shi = own + 1;
+    h->g = g;
+    h->Lx = Lx;
+    h->Ly = Ly;
+    h->prec = G.prec;
+    h->stream = (cudaStream_t)stream;
+    h->lay = make_layout(g, G.prec);
+    // the strip's rows and halos of the whole start configuration
+    HostState hs;
+    hs.loc.assign(8 * (size_t)g.C, kEmpty);
+    hs.cnt.assign((size_t)g.C, 0);
+    int64_t mine = 0;
+    for (int ly = 0; ly < g.my; ++ly) {
+        const int gy = ((g.row0 + ly) % G.g.my + G.g.my) % G.g.my;
+        for (int cx = 0; cx < g.mx; ++cx) {
+            const int64_t c = (int64_t)ly * g.mx + cx, gc = (int64_t)gy * g.mx + cx;
+            hs.cnt[c] = whole.cnt[gc];
+            for (int k = 0; k < 8; ++k) hs.loc[8 * c + k] = whole.loc[8 * gc + k];
+            if (ly >= 2 && ly <= own + 1) mine += whole.cnt[gc];
+        }
+    }
+    h->N = mine;
+    e = cuda_code(cudaMalloc((void**)&h->ws, h->lay.total));
+    h->own_ws = e == HDMC_OK;
+    if (!e) e = cuda_code(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    if (e) {
+        hdmc_destroy(h);
+        return e;
+    }
+    char* p = h->ws;
+    h->cells[0] = p;
+    p += h->lay.cells;
+    h->cells[1] = p;
+    p += h->lay.cells;
+    h->table = (SweepDraw*)p;
+    p += h->lay.table;
+    h->shift_table = (SweepDraw*)p;
+    p += h->lay.shift_table;
+    h->st = (DevState*)p;
+    h->g.check = &h->st->error;
+    p += h->lay.state;
+    h->partial = (unsigned long long*)p;
+    p += h->lay.partial;
+    h->hist = (unsigned long long*)p;
+    p += h->lay.hist;
+    h->edges2 = (double*)p;
+    p += h->lay.edges;
+    h->check = (unsigned long long*)p;
+    e = cuda_code(cudaMemset(h->ws + 2 * h->lay.cells, 0, h->lay.total - 2 * h->lay.cells));
+    if (!e) {
+        double E[kHistBins + 1];
+        squared_edges(sigma, E);
+        e = cuda_code(cudaMemcpy(h->edges2, E, sizeof(E), cudaMemcpyHostToDevice));
+    }
+    if (!e) e = upload(h, hs);
+    if (!e) e = cuda_code(cudaDeviceSynchronize());
+    if (e) {
+        hdmc_destroy(h);
+        return e;
+    }
+    *out = h;
+    return HDMC_OK;
+}
+
+int hdmc_strip_rows(hdmc_t* h, int32_t* first_row, int32_t* end_row) {
+    if (!h || !h->nstrips) return HDMC_EINVAL;
+    if (first_row) *first_row = h->r0;
+    if (end_row) *end_row = h->r1;
+    return HDMC_OK;
+}
+
+int hdmc_strip_subsweeps(hdmc_t* h) {
+    if (!h || !h->nstrips || h->pending) return HDMC_EINVAL;
+    LaunchCtx c = h->ctx(h->stream);
+    launch_draws(c, h->table, 1, true);
+    for (int k = 0; k < 4; ++k) {
+        if (h->prec == HDMC_FP64) launch_subsweep_f64(c, h->cells[h->cur], h->table, k);
+        else launch_subsweep_f32(c, h->cells[h->cur], h->table, k);
+    }
+    h->pending = true;
+    return cuda_code(cudaGetLastError());
+}
+
+int hdmc_strip_shift(hdmc_t* h) {
+    if (!h || !h->nstrips || !h->pending) return HDMC_EINVAL;
+    const LaunchCtx c = h->ctx(h->stream);
+    if (h->prec == HDMC_FP64) launch_shift_f64(c, h->cells[h->cur], h->cells[h->cur ^ 1], h->table);
+    else launch_shift_f32(c, h->cells[h->cur], h->cells[h->cur ^ 1], h->table);
+    h->cur ^= 1;
+    h->sweeps += 1;
+    h->pending = false;
+    return cuda_code(cudaGetLastError());
+}
+
+size_t hdmc_strip_row_bytes(const hdmc_t* h) {
+    if (!h || !h->nstrips) return 0;
+    return (size_t)h->g.mx * 8 * (h->prec == HDMC_FP64 ? sizeof(double) : sizeof(float));
+}
+
+int hdmc_strip_get_row(hdmc_t* h, int32_t which, void* buf) {
+    if (!h || !h->nstrips || !buf || which < 0 || which > 3) return HDMC_EINVAL;
+    return strip_copy_row(h, strip_local_row(h, which), buf, true);
+}
+
+int hdmc_strip_set_halo(hdmc_t* h, int32_t which, const void* buf) {
+    if (!h || !h->nstrips || !buf || which < 0 || which > 3) return HDMC_EINVAL;
+    return strip_copy_row(h, strip_local_row(h, which + 4), const_cast<void*>(buf), false);
+}
+
+int hdmc_strip_histogram(hdmc_t* h, uint64_t* hist, int64_t* n_samples) {
+    if (!h || !h->nstrips || !hist) return HDMC_EINVAL;
+    int e = check_device(h);
+    if (e) return e;
+    unsigned long long hh[kHistBins];
+    e = cuda_code(cudaMemcpy(hh, h->hist, sizeof(hh), cudaMemcpyDeviceToHost));
+    if (!e) e = cuda_code(cudaMemsetAsync(h->hist, 0, sizeof(hh), h->stream));
+    if (!e) e = cuda_code(cudaStreamSynchronize(h->stream));
+    if (e) return e;
+    for (int i = 0; i < kHistBins; ++i) hist[i] = hh[i];
+    if (n_samples) *n_samples = h->n_samples;
+    h->n_samples = 0;
+    return HDMC_OK;
+}
+
+int hdmc_pressure_fit(const uint64_t* hist, int64_t n_samples, int64_t N, double Lx, double Ly, double sigma,
+                      double* betaP_over_rho, double* g_contact) {
+    if (!hist || n_samples < 1 || N < 1 || !(Lx > 0) || !(Ly > 0) || !(sigma > 0)) return HDMC_EINVAL;
+    SysDesc d{};
+    d.g.sigma = sigma;
+    d.g.sig2 = sigma * sigma;
+    d.N = N;
+    d.Lx = Lx;
+    d.Ly = Ly;
+    unsigned long long hh[kHistBins];
+    for (int i = 0; i < kHistBins; ++i) hh[i] = hist[i];
+    double g0;
+    const double bp = pressure_from_hist(d, hh, n_samples, &g0);
+    if (betaP_over_rho) *betaP_over_rho = bp;
+    if (g_contact) *g_contact = g0;
+    return HDMC_OK;
 }
 
 int hdmc_build_flags(void) {

@@ -260,11 +260,11 @@ extern "C" {
 size_t hdmc_batch_workspace_bytes(int R, const int64_t* N, const double* Lx, const double* Ly, double sigma,
                                   int precision) {
     if (R < 1 || R > 65535 || !N || !Lx || !Ly) return 0;
-    if (precision != HDMC_FP64 && precision != HDMC_FP32_LOCAL) return 0;
+    if ((precision & 0xFF) != HDMC_FP64 && (precision & 0xFF) != HDMC_FP32_LOCAL) return 0;
     std::vector<SysDesc> sys(R);
     for (int r = 0; r < R; ++r)
         if (make_system(sys[r], N[r], Lx[r], Ly[r], sigma, 0.25, 4, 0, precision)) return 0;
-    return batch_layout(sys, precision).total;
+    return batch_layout(sys, precision & 0xFF).total;
 }
 
 int hdmc_batch_create(hdmc_batch_t** out, int R, const int64_t* N, const double* Lx, const double* Ly,
@@ -284,10 +284,10 @@ int hdmc_batch_create(hdmc_batch_t** out, int R, const int64_t* N, const double*
     hdmc_batch_t* b = new (std::nothrow) hdmc_batch_t();
     if (!b) return HDMC_ENOMEM;
     b->R = R;
-    b->prec = precision;
+    b->prec = sys[0].prec;   // the bare precision (without the cell rule)
     b->sys = sys;
     b->stream = (cudaStream_t)stream;
-    b->lay = batch_layout(sys, precision);
+    b->lay = batch_layout(sys, b->prec);
     b->counter_base.assign(4 * (size_t)R, 0);
     long long off = 0;
     for (int r = 0; r < R; ++r) {
@@ -419,6 +419,31 @@ int hdmc_batch_get_state(hdmc_batch_t* b, int r, double* local, uint8_t* counts)
     if (local) std::memcpy(local, hs.loc.data(), sizeof(double) * hs.loc.size());
     if (counts) std::memcpy(counts, hs.cnt.data(), hs.cnt.size());
     return HDMC_OK;
+}
+
+int hdmc_batch_set_state(hdmc_batch_t* b, int r, const double* local, const uint8_t* counts,
+                         const double origin[2], uint64_t sweeps_done) {
+    if (!b || r < 0 || r >= b->R || !local || !counts || !origin) return HDMC_EINVAL;
+    const SysDesc& d = b->sys[r];
+    HostState hs;
+    int e = state_from_local(d, local, counts, hs);
+    if (e) return e;
+    std::vector<char> raw;
+    pack(d, hs, raw);
+    e = cuda_code(cudaStreamSynchronize(b->stream));
+    if (!e)
+        e = cuda_code(cudaMemcpy((char*)b->arena[b->cur] + (size_t)b->cell_off[r] * 8 * d.coord_bytes(), raw.data(),
+                                 raw.size(), cudaMemcpyHostToDevice));
+    DevState ds;
+    if (!e) e = cuda_code(cudaMemcpy(&ds, b->sts + r, sizeof(ds), cudaMemcpyDeviceToHost));
+    if (e) return e;
+    ds.origin[0] = origin[0];
+    ds.origin[1] = origin[1];
+    ds.sweep_next = sweeps_done;
+    ds.error = 0;
+    e = cuda_code(cudaMemcpy(b->sts + r, &ds, sizeof(ds), cudaMemcpyHostToDevice));
+    if (!e) e = cuda_code(cudaDeviceSynchronize());
+    return e;
 }
 
 int hdmc_batch_counters(hdmc_batch_t* b, uint64_t* out) {

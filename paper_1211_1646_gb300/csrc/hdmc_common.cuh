@@ -69,9 +69,11 @@ __device__ __forceinline__ void fields21(const uint4 w, uint32_t f[6]) {
     f[4] = __funnelshift_r(w.z, w.w, 20) & M;
     f[5] = (w.w >> 9) & M;
 }
-// Odd multiples of 2^-21 in (-1,1).
+// Odd multiples of 2^-21 in (-1,1): (2f + 1 - 2^21) 2^-21, formed as
+// 2 (1 + f 2^-21) - 3 + 2^-21 from the binary32 1 + f 2^-21 (f in the top
+// of the significand); the FMA is exact, its result having 22 bits.
 __device__ __forceinline__ float sym21(uint32_t f) {
-    return (float)((int32_t)(2 * f + 1) - (1 << 21)) * 0x1p-21f;
+    return __fmaf_rn(__uint_as_float(0x3F800000u | (f << 2)), 2.0f, -3.0f + 0x1p-21f);
 }
 
 

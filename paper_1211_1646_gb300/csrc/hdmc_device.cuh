@@ -53,6 +53,11 @@ struct Geometry {
     uint32_t key0, key1;   // Philox key = seed
     uint32_t flags;        // kNoParticleShuffle | kNoSetShuffle (Table 1 controls); 0 = the method
     unsigned int* check;   // builds with -DHDMC_CHECK: device word that collects failed index checks
+    // Rows of a strip of a larger grid (spatial decomposition, Sec. 6); a
+    // whole system has row0 = 0 and both ranges [0, my-1].
+    int row0;              // global cell row of row 0 (random streams use global cell numbers)
+    int ylo, yhi;          // rows whose cells make trial moves
+    int slo, shi;          // rows the shift writes and the contact histogram counts
 };
 
 // Device error word bits: a cell received more than its slots (bit 0); a

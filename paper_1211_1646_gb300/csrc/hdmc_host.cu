@@ -24,16 +24,33 @@ int error_code(unsigned int device_error) {
     return HDMC_OK;
 }
 
-// Cell grid of a box: mx = largest even integer <= Lx/sigma (likewise my),
-// w = L/m; needs m >= 4 and w < sqrt(2) sigma (at most 4 disks per cell).
-bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy) {
+// Cells along one axis of length L.  Default rule: m = largest even integer
+// <= L/sigma (cells just wider than sigma).  HDMC_CELLS_SQRT2 (Sec. 3.1):
+// floor(L/(sqrt(2) sigma)) rounded up to the smallest even m > L/(sqrt(2)
+// sigma), the widest cells that still hold at most 4 centres (Fig. 3); it
+// must not make w < sigma.  m is even so that the checkerboard tiles the
+// periodic box (Eq. 1).  -1 if invalid.
+static int cells_along(double L, double sigma, int rule) {
+    const double q = std::floor(L / sigma);
+    if (q > 1.0e9) return -1;
+    int m = (int)q;
+    m -= m & 1;
+    if (rule == 1) {
+        int k = (int)(std::floor(L / (std::sqrt(2.0) * sigma)) + 1.0);
+        k += k & 1;
+        if (k > m) return -1;
+        m = k;
+    }
+    return m;
+}
+
+// Cell grid of a box: mx, my by the rule, w = L/m; needs m >= 4 and
+// w < sqrt(2) sigma (at most 4 disks per cell).
+bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy, int rule) {
     if (!(sigma > 0) || !(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly)) return false;
-    const double qx = std::floor(Lx / sigma), qy = std::floor(Ly / sigma);
-    if (qx > 1.0e9 || qy > 1.0e9) return false;
-    mx = (int)qx;
-    my = (int)qy;
-    mx -= mx & 1;
-    my -= my & 1;
+    if (rule < 0 || rule > 1) return false;
+    mx = cells_along(Lx, sigma, rule);
+    my = cells_along(Ly, sigma, rule);
     if (mx < 4 || my < 4) return false;
     wx = Lx / mx;
     wy = Ly / my;
@@ -44,9 +61,11 @@ int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, doubl
                 uint64_t seed, int precision) {
     int mx, my;
     double wx, wy;
+    const int rule = precision >> 8;   // HDMC_CELLS_SQRT2 or 0
+    precision &= 0xFF;
     if (N < 1 || nselect < 1 || nselect > 255) return HDMC_EINVAL;
     if (precision != HDMC_FP64 && precision != HDMC_FP32_LOCAL) return HDMC_EINVAL;
-    if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy)) return HDMC_EINVAL;
+    if (!make_grid(Lx, Ly, sigma, mx, my, wx, wy, rule)) return HDMC_EINVAL;
     if (!(dmove > 0) || !(dmove < 0.5 * wx) || !(dmove < 0.5 * wy)) return HDMC_EINVAL;
     if ((int64_t)mx * my * kSlots < N) return HDMC_EINVAL;
     if ((int64_t)mx * my >= (int64_t(1) << 32)) return HDMC_EINVAL;   // kernels index cells in 32 bits
@@ -70,6 +89,9 @@ int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, doubl
     g.nsel = nselect;
     g.key0 = (uint32_t)seed;
     g.key1 = (uint32_t)(seed >> 32);
+    g.row0 = 0;
+    g.ylo = g.slo = 0;
+    g.yhi = g.shi = my - 1;
     d.N = N;
     d.Lx = Lx;
     d.Ly = Ly;
@@ -204,6 +226,30 @@ bool any_overlap(const SysDesc& h, const HostState& hs) {
             }
         }
     return false;
+}
+
+// A caller's state (hdmc_get_state layout) checked and copied: counts <= 4,
+// occupied coordinates in [0, w) of the precision (binary32 values for a
+// binary32 system), N disks in all.  HDMC_EINVAL otherwise.
+int state_from_local(const SysDesc& d, const double* local, const uint8_t* counts, HostState& hs) {
+    const Geometry& g = d.g;
+    hs.loc.assign(8 * (size_t)g.C, kEmpty);
+    hs.cnt.assign(counts, counts + g.C);
+    int64_t total = 0;
+    for (int64_t c = 0; c < g.C; ++c) {
+        if (hs.cnt[c] > kSlots) return HDMC_EINVAL;
+        total += hs.cnt[c];
+        for (int j = 0; j < hs.cnt[c]; ++j) {
+            const double x = local[2 * (4 * c + j)], y = local[2 * (4 * c + j) + 1];
+            const bool fits = d.prec == HDMC_FP64 ? (x >= 0 && x < g.wx && y >= 0 && y < g.wy)
+                                                  : ((double)(float)x == x && (double)(float)y == y && x >= 0 &&
+                                                     (float)x < g.wxf && y >= 0 && (float)y < g.wyf);
+            if (!fits) return HDMC_EINVAL;
+            hs.loc[2 * (4 * c + j)] = x;
+            hs.loc[2 * (4 * c + j) + 1] = y;
+        }
+    }
+    return total == d.N ? HDMC_OK : HDMC_EINVAL;
 }
 
 // Canonical host state <-> set-major device cells (x0..x3 then y0..y3 per cell).

@@ -28,7 +28,8 @@ struct HostState {
 
 int cuda_code(cudaError_t e);
 int error_code(unsigned int device_error);   // device error word -> HDMC_E* (0: HDMC_OK)
-bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy);
+bool make_grid(double Lx, double Ly, double sigma, int& mx, int& my, double& wx, double& wy, int rule = 0);
+// precision: HDMC_FP64 or HDMC_FP32_LOCAL, optionally | HDMC_CELLS_SQRT2 (d.prec is the bare precision)
 int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, double dmove, int nselect,
                 uint64_t seed, int precision);
 bool lattice_shape(int64_t N, double Lx, double Ly, int64_t& nx, int64_t& ny);
@@ -37,6 +38,7 @@ void lattice_positions(int64_t N, double Lx, double Ly, double sigma, uint32_t k
 int bin_positions(const SysDesc& d, const double* xy, HostState& hs);
 bool any_overlap(const SysDesc& d, const HostState& hs);
 int start_state(const SysDesc& d, HostState& hs);   // hexagonal start, binned and checked
+int state_from_local(const SysDesc& d, const double* local, const uint8_t* counts, HostState& hs);
 void pack(const SysDesc& d, const HostState& hs, std::vector<char>& raw);
 void unpack(const SysDesc& d, const std::vector<char>& raw, HostState& hs);
 void squared_edges(double sigma, double* E);          // kHistBins + 1 values

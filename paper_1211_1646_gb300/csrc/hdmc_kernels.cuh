@@ -26,9 +26,11 @@ static __device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax
     st->origin[ax] = __dadd_rn(st->origin[ax], sd);
 }
 
-// Per-launch constants of the moving coordinate and the evaluation of one
-// disk: whether it stays in its cell, and its new coordinate (in its old
-// cell's frame if it stays, else in the frame of the cell it moves to).
+// Per-launch constants of the moving coordinate and the evaluation of the
+// disks seen by one new cell: stayer() for a disk of old c (does it stay, and
+// its new coordinate if it does), migrant() for a disk of old c + f (does it
+// leave c + f, and its coordinate in c's frame if it does).  Both apply the
+// same ownership test to a disk, so the two threads that see it agree.
 template <typename T> struct ShiftParams;
 
 // binary64 path: dp = x - sgn ds; stays iff 0 <= dp < w; a migrant's new
@@ -42,33 +44,30 @@ template <> struct ShiftParams<double> {
         wprev = Prm<double>::prev(w);
     }
     __device__ __forceinline__ double origin_step() const { return sd; }
-    __device__ __forceinline__ void disk(double x, bool& stay, double& v) const {
+    __device__ __forceinline__ void stayer(double x, bool& stay, double& v) const {
+        v = __dsub_rn(x, sd);
+        stay = Prm<double>::ge0(v) && Prm<double>::lt(v, w);
+    }
+    __device__ __forceinline__ void migrant(double x, bool& leave, double& v) const {
         const double dp = __dsub_rn(x, sd);
-        stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, w);
-        if (stay) {
-            v = dp;
-        } else {
-            v = __dadd_rn(dp, sw);
-            v = Prm<double>::lt(v, w) ? v : wprev;
-            v = Prm<double>::ge0(v) ? v : 0.0;
-        }
+        leave = !(Prm<double>::ge0(dp) && Prm<double>::lt(dp, w));
+        v = __dadd_rn(dp, sw);
+        v = Prm<double>::lt(v, w) ? v : wprev;
+        v = Prm<double>::ge0(v) ? v : 0.0;
     }
 };
 
 // binary32 rounding of the real number s + t + eta, |eta| <= mu, |s| >= |t|
 // (s, t binary32): r = RN32(s + t), and s + t = r + rho exactly (Fast2Sum).
-// All reals within mu of s + t round to r when rho stays more than mu inside
-// the rounding interval of r (half an ulp on either side, a quarter ulp below
-// a power of two); otherwise ok is cleared.
+// All reals within mu of s + t round to r when r is positive, not a power
+// of two, and rho stays more than mu inside its rounding interval (half an
+// ulp on either side); otherwise ok is cleared.
 __device__ __forceinline__ float rn32_certified(float s, float t, float mu, bool& ok) {
     const float r = __fadd_rn(s, t);
     const float rho = __fsub_rn(t, __fsub_rn(r, s));
     const uint32_t rb = __float_as_uint(r);
-    const uint32_t e = rb & 0x7F800000u;
-    const float h = __uint_as_float(e - (24u << 23));   // half an ulp of r (exponent field > 24)
-    const float hd = (rb & 0x7FFFFFu) ? h : 0.5f * h;    // below a power of two
-    ok = ok && (rb >> 31) == 0u && e > (24u << 23) &&
-         (rho >= 0.0f ? __fadd_rn(rho, mu) < h : __fsub_rn(mu, rho) < hd);
+    const float h = __uint_as_float((rb & 0x7F800000u) - (24u << 23));   // half an ulp of r
+    ok = (rb & 0x7FFFFFu) != 0u && rb > (25u << 23) && rb < 0x7F800000u && __fadd_rn(fabsf(rho), mu) < h;
     return r;
 }
 
@@ -86,12 +85,14 @@ __device__ __forceinline__ float rn32_certified(float s, float t, float mu, bool
 // (s - W) + t (s - W exact, Sterbenz) with the bound mu = 2^-43 W on eta,
 // the binary32 rounding of the tails and the binary64 roundings of the
 // remap.  The rest, about one disk in 10^5, is evaluated with binary64
-// instructions.
+// instructions; only that branch touches the binary64 constants.
 template <> struct ShiftParams<float> {
     float d1, d2, wf, wprev, tau, mu;
+    int sgn;
     bool fast;   // the bounds need cell widths far above the binary32 underflow range
-    double sd, W, sW;
-    __device__ ShiftParams(const Geometry& g, const SweepDraw& r, int ax, int sgn) {
+    const SweepDraw* draw;
+    __device__ ShiftParams(const Geometry& g, const SweepDraw& r, int ax, int sgn_) {
+        sgn = sgn_;
         wf = ax ? g.wyf : g.wxf;
         wprev = Prm<float>::prev(wf);
         d1 = sgn > 0 ? r.dsf : -r.dsf;
@@ -99,36 +100,50 @@ template <> struct ShiftParams<float> {
         tau = __fmul_rn(wf, 0x1p-20f);
         mu = __fmul_rn(wf, 0x1p-43f);
         fast = wf > 0x1p-60f;
-        W = (double)wf;
-        sd = sgn > 0 ? r.ds : -r.ds;
-        sW = sgn > 0 ? W : -W;
+        draw = &r;
     }
-    __device__ __forceinline__ double origin_step() const { return sd; }
-    __device__ __forceinline__ void disk(float x, bool& stay, float& v) const {
-        const float s = __fsub_rn(x, d1);
+    __device__ __forceinline__ double origin_step() const { return sgn > 0 ? draw->ds : -draw->ds; }
+    // s = RN32(x - d1) and t: x - sgn ds = s + t + eta; sw = RN32(s - W)
+    __device__ __forceinline__ void split(float x, float& s, float& t, float& sw, bool& sure) const {
+        s = __fsub_rn(x, d1);
         const float bb = __fsub_rn(s, x);   // TwoSum(x, -d1): s + e = x - d1 exactly
         const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-d1, bb));
-        const float t = __fsub_rn(e, d2);
-        const float sw = __fsub_rn(s, wf);
-        bool ok = fast && fabsf(s) > tau && fabsf(sw) > tau;
+        t = __fsub_rn(e, d2);
+        sw = __fsub_rn(s, wf);
+        sure = fast && fabsf(s) > tau && fabsf(sw) > tau;   // the ownership test is decided by s
+    }
+    __device__ __forceinline__ void exact(float x, bool& stay, float& v) const {   // binary64 instructions
+        const double W = (double)wf;
+        const double dp = __dsub_rn((double)x, sgn > 0 ? draw->ds : -draw->ds);
+        stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, W);
+        v = __double2float_rn(stay ? dp : __dadd_rn(dp, sgn > 0 ? W : -W));
+    }
+    __device__ __forceinline__ void stayer(float x, bool& stay, float& v) const {
+        float s, t, sw;
+        bool sure, ok;
+        split(x, s, t, sw, sure);
         stay = s > 0.0f && sw < 0.0f;
-        if (!stay) {
-            if (s < 0.0f) {   // +f migrant: (s + W) + t
-                const float s2 = __fadd_rn(s, wf);
-                const float e2 = __fsub_rn(s, __fsub_rn(s2, wf));
-                v = rn32_certified(s2, __fadd_rn(e2, t), mu, ok);
-            } else {          // -f migrant: (s - W) + t
-                v = rn32_certified(sw, t, mu, ok);
-            }
-        } else {
-            v = rn32_certified(s, t, mu, ok);
-        }
-        if (!ok) {   // binary64 instructions, exactly as the rule reads
-            const double dp = __dsub_rn((double)x, sd);
-            stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, W);
-            v = __double2float_rn(stay ? dp : __dadd_rn(dp, sW));
-        }
+        v = rn32_certified(s, t, mu, ok);
+        if (!sure || (stay && !ok)) exact(x, stay, v);
         v = v < wf ? v : wprev;   // v >= 0, or -0 from a -0 stayer as the binary64 rule gives
+    }
+    __device__ __forceinline__ void migrant(float x, bool& leave, float& v) const {
+        float s, t, sw;
+        bool sure, ok;
+        split(x, s, t, sw, sure);
+        leave = !(s > 0.0f && sw < 0.0f);
+        if (sgn > 0) {   // (s + W) + t, s + W by Fast2Sum (warp-uniform branch)
+            const float s2 = __fadd_rn(s, wf);
+            v = rn32_certified(s2, __fadd_rn(__fsub_rn(s, __fsub_rn(s2, wf)), t), mu, ok);
+        } else {         // (s - W) + t, s - W exact
+            v = rn32_certified(sw, t, mu, ok);
+        }
+        if (!sure || (leave && !ok)) {
+            bool stay;
+            exact(x, stay, v);
+            leave = !stay;
+        }
+        v = v < wf ? v : wprev;
     }
 };
 
@@ -145,6 +160,7 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     if (hx == 0 && hy == 0 && q == 0) add_origin(st, ax, P.origin_step());
     if (hx >= g.hx || hy >= g.hy) return;
     const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
+    if (cy < g.slo || cy > g.shi) return;   // a strip's halo rows are not its own
     const int ncx = ax ? cx : wrap(cx + sgn, g.mx);
     const int ncy = ax ? wrap(cy + sgn, g.my) : cy;
     const long long idx = (long long)q * g.cq + (long long)hy * g.hx + hx;
@@ -159,33 +175,29 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
         if (Prm<T>::ge0(o.x[j])) {
             bool stay;
             T v;
-            P.disk(ax ? o.y[j] : o.x[j], stay, v);
-            if (stay) {
-                const T vx = ax ? o.x[j] : v, vy = ax ? v : o.y[j];
+            P.stayer(ax ? o.y[j] : o.x[j], stay, v);
+            const T vx = ax ? o.x[j] : v, vy = ax ? v : o.y[j];
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    r.x[s] = (kept == s) ? vx : r.x[s];
-                    r.y[s] = (kept == s) ? vy : r.y[s];
-                }
-                ++kept;
+            for (int s = 0; s <= j; ++s) {
+                r.x[s] = (stay && kept == s) ? vx : r.x[s];
+                r.y[s] = (stay && kept == s) ? vy : r.y[s];
             }
+            kept += stay;
         }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {   // migrants of old c + f
         if (Prm<T>::ge0(b.x[j])) {
-            bool stay;
+            bool leave;
             T v;
-            P.disk(ax ? b.y[j] : b.x[j], stay, v);
-            if (!stay) {
-                const T vx = ax ? b.x[j] : v, vy = ax ? v : b.y[j];
+            P.migrant(ax ? b.y[j] : b.x[j], leave, v);
+            const T vx = ax ? b.x[j] : v, vy = ax ? v : b.y[j];
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    r.x[s] = (kept == s) ? vx : r.x[s];
-                    r.y[s] = (kept == s) ? vy : r.y[s];
-                }
-                ++kept;
+            for (int s = 0; s < 4; ++s) {
+                r.x[s] = (leave && kept == s) ? vx : r.x[s];
+                r.y[s] = (leave && kept == s) ? vy : r.y[s];
             }
+            kept += leave;
         }
     }
     if (kept > 4) atomicOr(&st->error, kErrOverflow);
@@ -270,12 +282,12 @@ __device__ __forceinline__ void hist_cells(const Geometry& g, const T* __restric
     const int lane = threadIdx.x;
     const int hx = bx * kHistBX + threadIdx.x;
     const int hy = by * kHistBY + threadIdx.y;
-    const bool live = hx < g.hx && hy < g.hy;
+    const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
+    const bool live = hx < g.hx && hy < g.hy && cy >= g.slo && cy <= g.shi;   // own rows only
     uint32_t* sq = squeue[threadIdx.y];
     Cell<T> own;
 #pragma unroll
     for (int j = 0; j < 4; ++j) own.x[j] = own.y[j] = T(kEmpty);
-    const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
     if (live) load_cell_ro(cells + 8 * ((long long)q * g.cq + (long long)hy * g.hx + hx), own);
     const bool any = __any_sync(0xffffffffu, Prm<T>::ge0(own.x[0]));
     const bool own23 = __any_sync(0xffffffffu, Prm<T>::ge0(own.x[2]));

@@ -65,8 +65,8 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const uint32_t sweep = draw->sweep;
     const int hx = bx * 32 + threadIdx.x;
     const int hy = by * ROWS + threadIdx.y;
-    const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
+    const bool live = hx < g.hx && hy < g.hy && cy >= g.ylo && cy <= g.yhi;
     const Neighbourhood nbh(g, Q, hx, hy, live);
 
     // 1. loads
@@ -91,7 +91,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     }
 
     // 2. directions of the first chunk (the cell's trial stream)
-    const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+    const uint32_t cell = (uint32_t)(cy + g.row0) * (uint32_t)g.mx + (uint32_t)cx;   // global cell number
     const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
     uint32_t F[6];
     fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
@@ -315,8 +315,8 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
     const uint32_t sweep = draw->sweep;
     const int hx = bx * 32 + threadIdx.x;
     const int hy = by * ROWS + threadIdx.y;
-    const bool live = hx < g.hx && hy < g.hy;
     const int cx = 2 * hx + (Q & 1), cy = 2 * hy + (Q >> 1);
+    const bool live = hx < g.hx && hy < g.hy && cy >= g.ylo && cy <= g.yhi;
     const Neighbourhood nbh(g, Q, hx, hy, live);
 
     Cell<double> own;
@@ -347,7 +347,7 @@ __device__ __forceinline__ void subsweep_f64(const Geometry& g, double* __restri
 
     unsigned int n_tr = 0, n_acc = 0, n_leave = 0;
     if (n > 0) {
-        const uint32_t cell = (uint32_t)cy * (uint32_t)g.mx + (uint32_t)cx;
+        const uint32_t cell = (uint32_t)(cy + g.row0) * (uint32_t)g.mx + (uint32_t)cx;   // global cell number
         const uint32_t setbits = (uint32_t)Q << 24;
         if (n >= 2 && !(g.flags & kNoParticleShuffle)) {
             WordStream s(g.key0, g.key1, sweep, cell, (kDomShuffle << 28) | setbits);

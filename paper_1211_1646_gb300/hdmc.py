@@ -15,6 +15,7 @@ from . import build as _build
 HDMC_OK, HDMC_EINVAL, HDMC_ECUDA, HDMC_EOVERFLOW, HDMC_EOVERLAP, HDMC_ETIMEOUT, HDMC_ENOMEM, HDMC_ECHECK = range(8)
 HDMC_BUILD_CHECK = 1
 HDMC_FP64, HDMC_FP32_LOCAL = 0, 1
+HDMC_CELLS_SQRT2 = 0x100
 HDMC_EMPTY_SLOT = -1.0e4
 HDMC_HIST_BINS = 200
 HDMC_NOALLOC_MAX_BINS = 1024
@@ -60,6 +61,18 @@ SIGNATURES = {
     "hdmc_profile_stages": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
     "hdmc_histogram_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int32, ctypes.c_double, _u64p, _vp]),
+    "hdmc_strip_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_int32, ctypes.c_int32, _vp]),
+    "hdmc_strip_rows": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "hdmc_strip_subsweeps": (ctypes.c_int, [_vp]),
+    "hdmc_strip_shift": (ctypes.c_int, [_vp]),
+    "hdmc_strip_row_bytes": (ctypes.c_size_t, [_vp]),
+    "hdmc_strip_get_row": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "hdmc_strip_set_halo": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "hdmc_strip_histogram": (ctypes.c_int, [_vp, _u64p, _i64p]),
+    "hdmc_pressure_fit": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _f64p, _f64p]),
     "hdmc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, _i64p, _f64p, _f64p, ctypes.c_double,
                                                      ctypes.c_int]),
     "hdmc_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, _f64p, _f64p, ctypes.c_double,
@@ -68,6 +81,7 @@ SIGNATURES = {
     "hdmc_batch_sample": (ctypes.c_int, [_vp]),
     "hdmc_batch_pressure": (ctypes.c_int, [_vp, _f64p, _f64p, _u64p, _i64p]),
     "hdmc_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _u8p]),
+    "hdmc_batch_set_state": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _u8p, _f64p, ctypes.c_uint64]),
     "hdmc_batch_counters": (ctypes.c_int, [_vp, _u64p]),
     "hdmc_batch_psi6": (ctypes.c_int, [_vp, ctypes.c_double, _f64p]),
     "hdmc_batch_snapshot_bytes": (ctypes.c_size_t, [_vp]),
@@ -144,10 +158,20 @@ def _p(a, t):
 
 
 def _precision(p):
+    """HDMC_FP64 / HDMC_FP32_LOCAL from a name or value; an int may carry HDMC_CELLS_SQRT2."""
+    if isinstance(p, int) and (p & ~0xFF) == HDMC_CELLS_SQRT2 and (p & 0xFF) in _PRECISIONS:
+        return p
     try:
         return _PRECISIONS[p]
     except KeyError:
         raise ValueError("precision must be 'fp64' or 'fp32'") from None
+
+
+def with_cells(precision, cells):
+    """precision for the library calls with cell rule cells ('sigma' or 'sqrt2')."""
+    if cells not in ("sigma", "sqrt2"):
+        raise ValueError("cells must be 'sigma' or 'sqrt2'")
+    return _precision(precision) | (HDMC_CELLS_SQRT2 if cells == "sqrt2" else 0)
 
 
 # ---- one Python function per C entry point ----------------------------------------
@@ -324,6 +348,55 @@ def hdmc_histogram_noalloc(dev_local, mx, my, wx, wy, sigma, nbins, dr, stream=N
     return hist
 
 
+def hdmc_strip_create(N, Lx, Ly, sigma, d, nselect, seed, precision, nstrips, strip, stream=None):
+    h = _vp()
+    _check(lib().hdmc_strip_create(ctypes.byref(h), N, Lx, Ly, sigma, d, nselect, seed & 0xFFFFFFFFFFFFFFFF,
+                                   _precision(precision), nstrips, strip, stream), "hdmc_strip_create")
+    return h
+
+
+def hdmc_strip_rows(h):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().hdmc_strip_rows(h, ctypes.byref(a), ctypes.byref(b)), "hdmc_strip_rows")
+    return a.value, b.value
+
+
+def hdmc_strip_subsweeps(h):
+    _check(lib().hdmc_strip_subsweeps(h), "hdmc_strip_subsweeps")
+
+
+def hdmc_strip_shift(h):
+    _check(lib().hdmc_strip_shift(h), "hdmc_strip_shift")
+
+
+def hdmc_strip_row_bytes(h):
+    return int(lib().hdmc_strip_row_bytes(h))
+
+
+def hdmc_strip_get_row(h, which, buf_ptr):
+    _check(lib().hdmc_strip_get_row(h, which, buf_ptr), "hdmc_strip_get_row")
+
+
+def hdmc_strip_set_halo(h, which, buf_ptr):
+    _check(lib().hdmc_strip_set_halo(h, which, buf_ptr), "hdmc_strip_set_halo")
+
+
+def hdmc_strip_histogram(h):
+    hist = np.zeros(HDMC_HIST_BINS, dtype=np.uint64)
+    ns = ctypes.c_int64()
+    _check(lib().hdmc_strip_histogram(h, _p(hist, _u64p), ctypes.byref(ns)), "hdmc_strip_histogram")
+    return hist, ns.value
+
+
+def hdmc_pressure_fit(hist, n_samples, N, Lx, Ly, sigma=1.0):
+    """(beta P / rho, g(sigma+)) of a contact histogram (Sec. 4)."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    bp, g0 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hdmc_pressure_fit(_p(h, _u64p), n_samples, N, Lx, Ly, sigma, ctypes.byref(bp), ctypes.byref(g0)),
+           "hdmc_pressure_fit")
+    return bp.value, g0.value
+
+
 def hdmc_destroy(h):
     if h is not None and h.value:
         lib().hdmc_destroy(h)
@@ -374,6 +447,14 @@ def hdmc_batch_get_state(b, r, C):
     cnt = np.zeros(C, dtype=np.uint8)
     _check(lib().hdmc_batch_get_state(b, r, _p(loc, _f64p), _p(cnt, _u8p)), "hdmc_batch_get_state")
     return loc.reshape(C, 4, 2), cnt
+
+
+def hdmc_batch_set_state(b, r, local, counts, origin, sweeps_done):
+    loc = np.ascontiguousarray(local, dtype=np.float64).reshape(-1)
+    cnt = np.ascontiguousarray(counts, dtype=np.uint8)
+    org = np.ascontiguousarray(origin, dtype=np.float64)
+    _check(lib().hdmc_batch_set_state(b, r, _p(loc, _f64p), _p(cnt, _u8p), _p(org, _f64p), sweeps_done),
+           "hdmc_batch_set_state")
 
 
 def hdmc_batch_counters(b, R):
@@ -460,12 +541,13 @@ class System:
     """
 
     def __init__(self, N, Lx, Ly, sigma=1.0, d=0.1, nselect=4, seed=1, precision="fp32", xy=None,
-                 stream=None, device=None):
+                 stream=None, device=None, cells="sigma"):
         import torch
 
         self.N, self.Lx, self.Ly, self.sigma = N, Lx, Ly, sigma
-        self.precision = _precision(precision)
-        nbytes = hdmc_workspace_bytes(N, Lx, Ly, sigma, self.precision)
+        self.precision = _precision(precision) & 0xFF
+        mode = with_cells(self.precision, cells)   # precision argument with the cell rule
+        nbytes = hdmc_workspace_bytes(N, Lx, Ly, sigma, mode)
         if nbytes == 0:
             raise HDMCError(HDMC_EINVAL, "hdmc_workspace_bytes")
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -476,7 +558,7 @@ class System:
             stream = torch.cuda.current_stream(dev).cuda_stream
         self._stream = stream
         self.h = None
-        self.h = hdmc_create(N, Lx, Ly, sigma, d, nselect, seed, self.precision, ptr, nbytes, stream)
+        self.h = hdmc_create(N, Lx, Ly, sigma, d, nselect, seed, mode, ptr, nbytes, stream)
         info = hdmc_info(self.h)
         self.mx, self.my, self.wx, self.wy = info["mx"], info["my"], info["wx"], info["wy"]
         self.C = self.mx * self.my
@@ -569,15 +651,16 @@ class Batch:
     (e.g. workloads.Workload).  Workspace and stream from PyTorch as in System.
     """
 
-    def __init__(self, replicas, sigma=1.0, precision="fp32", stream=None, device=None):
+    def __init__(self, replicas, sigma=1.0, precision="fp32", stream=None, device=None, cells="sigma"):
         import torch
 
         self.R = len(replicas)
         self.N = [int(w.N) for w in replicas]
-        self.precision = _precision(precision)
+        self.precision = _precision(precision) & 0xFF
+        mode = with_cells(self.precision, cells)
         Lx = [w.Lx for w in replicas]
         Ly = [w.Ly for w in replicas]
-        nbytes = hdmc_batch_workspace_bytes(self.N, Lx, Ly, sigma, self.precision)
+        nbytes = hdmc_batch_workspace_bytes(self.N, Lx, Ly, sigma, mode)
         if nbytes == 0:
             raise HDMCError(HDMC_EINVAL, "hdmc_batch_workspace_bytes")
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -587,7 +670,7 @@ class Batch:
             stream = torch.cuda.current_stream(dev).cuda_stream
         self.b = None
         self.b = hdmc_batch_create(self.N, Lx, Ly, sigma, [w.d for w in replicas], [w.nselect for w in replicas],
-                                   [w.seed for w in replicas], self.precision, ptr, nbytes, stream)
+                                   [w.seed for w in replicas], mode, ptr, nbytes, stream)
         self.grids = [hdmc_batch_info(self.b, r) for r in range(self.R)]
 
     def close(self):
@@ -616,6 +699,9 @@ class Batch:
 
     def counters(self):
         return hdmc_batch_counters(self.b, self.R)
+
+    def set_state(self, r, local, counts, origin, sweeps_done):
+        hdmc_batch_set_state(self.b, r, local, counts, origin, sweeps_done)
 
     def origin(self, r):
         return hdmc_batch_info(self.b, r)["origin"]

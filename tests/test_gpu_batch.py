@@ -97,6 +97,26 @@ def test_batch_matches_oracle_and_pressure():
         assert abs(bp[r] - bp_ref) < 1e-9 * abs(bp_ref)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_paper_cell_rule(prec):
+    # replicas with the Sec. 3.1 cells (just below sqrt(2) sigma), each the
+    # oracle's chain on that grid, bit for bit
+    from paper_1211_1646_gb300 import hdmc
+    reps = _replicas()
+    b = hdmc.Batch(reps, precision=prec, cells="sqrt2")
+    orcs = [O.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, w.seed, O.FP64 if prec == "fp64" else O.FP32,
+                     cells=O.CELLS_SQRT2) for w in reps]
+    for r, o in enumerate(orcs):
+        assert (b.grids[r]["mx"], b.grids[r]["my"]) == (o.mx, o.my)
+    b.sweep(20)
+    for o in orcs:
+        o.sweep(20)
+    for r, o in enumerate(orcs):
+        assert np.array_equal(b.state(r)[1], o.state()[1])
+        assert np.array_equal(b.state(r)[0], o.state()[0])
+        assert np.array_equal(b.counters()[r], o.counters())
+
+
 def test_batch_autotune_and_invariants():
     from scipy.spatial import cKDTree
     from paper_1211_1646_gb300 import hdmc

@@ -237,6 +237,23 @@ def test_shift_edge_cases(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_cell_rule(prec):
+    # HDMC_CELLS_SQRT2 (Sec. 3.1 cell width just below sqrt(2) sigma): the same
+    # chain as the oracle with that grid, bit for bit
+    from paper_1211_1646_gb300 import hdmc
+    L = W.square_box(65536, 0.708)
+    g = hdmc.System(65536, L[0], L[1], 1.0, 0.1, 4, 9, prec, cells="sqrt2")
+    r = O.System(65536, L[0], L[1], 1.0, 0.1, 4, 9, PREC[prec], cells=O.CELLS_SQRT2)
+    assert (g.mx, g.my) == (r.mx, r.my) == (192, 192)
+    _same(g, r, "start")
+    g.sweep(20)
+    r.sweep(20)
+    _same(g, r, "after 20 sweeps")
+    _, _, hist, _ = g.pressure()
+    assert np.array_equal(hist, r.histogram(200, 1e-4))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_contact_histogram_and_pressure(prec):
     w = W.n65536_phi070()
     g, r = _pair(w, prec)

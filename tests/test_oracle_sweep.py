@@ -495,3 +495,26 @@ def test_inactive_bands_make_no_moves():
     with pytest.raises(ValueError):
         O.System(w.N, w.Lx, w.Ly, 1.0, w.d, 4, 9, O.FP64).set_strips(17)   # my = 32 < 2 x 17
 
+
+def test_paper_cell_rule():
+    # Sec. 3.1: m = floor(L / (sqrt(2) sigma)) rounded up, here to the next
+    # even integer (the checkerboard on a periodic box): the widest cells
+    # below sqrt(2) sigma, which still hold at most four centres (Fig. 3).
+    for L in (30.0, 100.0, 269.63, 1152.45):
+        mx, my, wx, wy = O.grid(L, L, 1.0, O.CELLS_SQRT2)
+        assert mx % 2 == 0 and 1.0 <= wx < math.sqrt(2.0)
+        assert L / (mx - 2) >= math.sqrt(2.0)            # two fewer cells would be too wide
+        assert O.grid(L, L)[0] >= mx
+    w = W.square_box(65536, 0.708)
+    assert O.grid(w[0], w[1], 1.0, O.CELLS_SQRT2)[0] == 192   # N = 256^2, phi = 0.708
+    w = W.square_box(16384, 0.708)
+    for prec in (O.FP64, O.FP32):
+        s = O.System(16384, w[0], w[1], 1.0, 0.1, 4, 2, prec, cells=O.CELLS_SQRT2)
+        s.sweep(40)
+        _, cnt = s.state()
+        Lx, Ly = s.box()
+        # binary32 positions re-rounded by the shift may sit a hair inside contact
+        assert O.close_pairs(s.positions(), Lx, Ly, R_MIN[prec]) == 0
+        assert int(cnt.sum()) == 16384 and cnt.max() <= 4
+        assert cnt.mean() > 1.7                           # about 1.8 disks per cell (0.9 with the default rule)
+
