@@ -461,7 +461,7 @@ def run_hdmc(args, rank, world, dist):
             s3 = hdmc.System3(w3.N, w3.L, 1.0, w3.d, w3.nselect, seed, prec)
             t3, ms3, p3 = timed_steps(s3, nsteps, 1)
             ms3 = max_over_ranks(ms3)
-            sub3, shift3 = s3.profile_sweeps(8)
+            sub3, shift3 = s3.profile_stages(16)   # in-step: runs of sub-sweeps / shifts, as in the step
             # algorithmic bytes of one sub-sweep launch, live data only: every
             # sphere read once (the neighbourhoods of the active cells cover
             # the grid) and the active set's spheres (one eighth) written
@@ -474,7 +474,8 @@ def run_hdmc(args, rank, world, dist):
                 leg["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                                    "frac": ach / hbm_peak, "traffic": profiled_traffic_spheres(),
                                    "kernel": "k_sub3<float>", "peak_kind": peak_kind,
-                                   "ms_per_launch": sub3, "algorithmic_bytes_per_launch": bytes3}
+                                   "ms_per_launch": sub3, "ms_per_launch_note": "in-step: mean over a run of "
+                                   "sub-sweep launches", "algorithmic_bytes_per_launch": bytes3}
                 tpl3 = t3 / nsteps / (SWEEPS_PER_STEP * 8)
                 ops3 = sum(SPHERE_ALU_OPS_PER_TRIAL.values())
                 ach3 = ops3 * tpl3 / (sub3 / 1e3) / 1e12

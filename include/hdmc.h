@@ -594,6 +594,14 @@ int hdmc3_sync(hdmc3_t *h);
  * one shift launch (nullable).  Synchronises. */
 int hdmc3_profile_sweeps(hdmc3_t *h, int64_t n, double *ms_subsweep, double *ms_shift);
 
+/* In-step timing of the three-dimensional sweep, as hdmc_profile_stages:
+ * n sweeps of the draws and eight sub-sweeps without shifts, then n sweeps of
+ * the draws and the shift, each run timed as a whole with CUDA events on the
+ * handle's stream; mean milliseconds per sub-sweep and per shift launch
+ * (each nullable).  The configuration stays legal, the trajectory is not
+ * that of hdmc3_sweep.  n >= 1.  Synchronises. */
+int hdmc3_profile_stages(hdmc3_t *h, int64_t n, double *ms_subsweep, double *ms_shift);
+
 /* Frees the handle. */
 void hdmc3_destroy(hdmc3_t *h);
 

@@ -834,6 +834,46 @@ int hdmc3_profile_sweeps(hdmc3_t* h, int64_t n, double* ms_subsweep, double* ms_
     return finish3(h);
 }
 
+int hdmc3_profile_stages(hdmc3_t* h, int64_t n, double* ms_subsweep, double* ms_shift) {
+    if (!h || n < 1) return HDMC_EINVAL;
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return HDMC_ECUDA;
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return HDMC_ECUDA;
+    }
+    double per[3] = {0.0, 0.0, 0.0};
+    int e = HDMC_OK;
+    for (int stage = 1; stage <= 2 && !e; ++stage) {
+        // stage 1: the draws and eight sub-sweeps of each sweep, no shift;
+        // stage 2: the draws and the shift of each sweep
+        cudaEventRecord(ev[0], h->stream);
+        for (int64_t done = 0; done < n;) {
+            const int cnt = (int)std::min<int64_t>(kDrawChunk3, n - done);
+            k_draws3<<<1, kDrawChunk3, 0, h->stream>>>(h->g, h->table, (uint32_t)h->sweeps, cnt, 1);
+            for (int j = 0; j < cnt; ++j) {
+                if (stage == 1)
+                    for (int k = 0; k < 8; ++k) launch_sub3(h, j, k);
+                else
+                    launch_shift3(h, j);
+                h->sweeps += 1;
+            }
+            done += cnt;
+        }
+        cudaEventRecord(ev[1], h->stream);
+        e = cuda_code(cudaEventSynchronize(ev[1]));
+        float ms = 0.f;
+        if (!e) e = cuda_code(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        per[stage] = (double)ms / (double)(n * (stage == 1 ? 8 : 1));
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e) return e;
+    if (ms_subsweep) *ms_subsweep = per[1];
+    if (ms_shift) *ms_shift = per[2];
+    return finish3(h);
+}
+
 int hdmc3_shift(hdmc3_t* h) {
     if (!h) return HDMC_EINVAL;
     k_draws3<<<1, 1, 0, h->stream>>>(h->g, h->table + kDrawChunk3, (uint32_t)h->shifts, 1, 0);

@@ -117,6 +117,7 @@ SIGNATURES = {
     "hdmc3_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hdmc3_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hdmc3_profile_sweeps": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
+    "hdmc3_profile_stages": (ctypes.c_int, [_vp, ctypes.c_int64, _f64p, _f64p]),
     "hdmc3_destroy": (None, [_vp]),
 }
 
@@ -844,6 +845,12 @@ def hdmc3_profile_sweeps(h, n):
     _check(lib().hdmc3_profile_sweeps(h, n, ctypes.byref(a), ctypes.byref(b)), "hdmc3_profile_sweeps")
     return a.value, b.value
 
+def hdmc3_profile_stages(h, n):
+    """Mean ms per (sub-sweep, shift) launch in runs of n sweeps of one stage each."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().hdmc3_profile_stages(h, n, ctypes.byref(a), ctypes.byref(b)), "hdmc3_profile_stages")
+    return a.value, b.value
+
 
 def hdmc3_destroy(h):
     if h is not None and h.value:
@@ -933,6 +940,9 @@ class System3:
 
     def profile_sweeps(self, n):
         return hdmc3_profile_sweeps(self.h, n)
+
+    def profile_stages(self, n):
+        return hdmc3_profile_stages(self.h, n)
 
     def box(self):
         """Periodic box of the precision's geometry (binary32 cell widths in fp32)."""
