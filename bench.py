@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-replica batch leg")
     ap.add_argument("--no-n4m", action="store_true", help="skip the N=4M legs")
     ap.add_argument("--no-spheres", action="store_true", help="skip the hard-sphere (3-d) legs")
-    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres"],
+    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres", "batch64"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
@@ -61,6 +61,16 @@ def ncu_case(args):
     import torch
     from paper_1211_1646_gb300 import build, hdmc, workloads
     build.build()
+    if args.ncu_case == "batch64":
+        b = hdmc.Batch(workloads.batch64(), precision="fp32")
+        b.set_rows(1)
+        hdmc.hdmc_batch_set_nselect(b.b, [8] * b.R)   # the autotuner's choice for this workload
+        b.sweep(3)
+        b.sample()
+        b.pressure()
+        torch.cuda.synchronize()
+        print("ncu case batch64 done: %d replicas, %d disks" % (b.R, sum(b.N)))
+        return
     if args.ncu_case == "spheres":
         w = workloads.spheres_n1m_phi049(args.precision)
         s = hdmc.System3(w.N, w.L, 1.0, w.d, w.nselect, 1, args.precision)
