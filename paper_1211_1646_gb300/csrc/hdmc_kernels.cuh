@@ -20,10 +20,11 @@ namespace hdmc {
 // lands in exactly one cell (Sec. 3.2).  A re-expressed value that rounds
 // onto the upper edge is clamped below it.
 //
-// Grid origin O += f*ds (one thread per shift), binary64.  Kept out of line
-// so that the binary64 addition stays in that one thread.
-static __device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax, double sd) {
-    st->origin[ax] = __dadd_rn(st->origin[ax], sd);
+// Grid origin O += f*ds (one thread per shift), binary64: ds added or
+// subtracted (the same rounding as adding -ds).  Kept out of line so that
+// the binary64 instruction stays in that one thread.
+static __device__ __noinline__ void add_origin(DevState* __restrict__ st, int ax, int sgn, double ds) {
+    st->origin[ax] = sgn > 0 ? __dadd_rn(st->origin[ax], ds) : __dsub_rn(st->origin[ax], ds);
 }
 
 // Per-launch constants of the moving coordinate and the evaluation of the
@@ -37,13 +38,15 @@ template <typename T> struct ShiftParams;
 // coordinate dp + sgn w, clamped into [0, w).
 template <> struct ShiftParams<double> {
     double sd, w, sw, wprev;
+    const SweepDraw* draw;
     __device__ ShiftParams(const Geometry& g, const SweepDraw& r, int ax, int sgn) {
+        draw = &r;
         w = ax ? g.wy : g.wx;
         sd = sgn > 0 ? r.ds : -r.ds;
         sw = sgn > 0 ? w : -w;
         wprev = Prm<double>::prev(w);
     }
-    __device__ __forceinline__ double origin_step() const { return sd; }
+    __device__ __forceinline__ double origin_ds() const { return draw->ds; }
     __device__ __forceinline__ void stayer(double x, bool& stay, double& v) const {
         v = __dsub_rn(x, sd);
         stay = Prm<double>::ge0(v) && Prm<double>::lt(v, w);
@@ -102,7 +105,7 @@ template <> struct ShiftParams<float> {
         fast = wf > 0x1p-60f;
         draw = &r;
     }
-    __device__ __forceinline__ double origin_step() const { return sgn > 0 ? draw->ds : -draw->ds; }
+    __device__ __forceinline__ double origin_ds() const { return draw->ds; }
     // s = RN32(x - d1) and t: x - sgn ds = s + t + eta; sw = RN32(s - W)
     __device__ __forceinline__ void split(float x, float& s, float& t, float& sw, bool& sure) const {
         s = __fsub_rn(x, d1);
@@ -112,11 +115,17 @@ template <> struct ShiftParams<float> {
         sw = __fsub_rn(s, wf);
         sure = fast && fabsf(s) > tau && fabsf(sw) > tau;   // the ownership test is decided by s
     }
-    __device__ __forceinline__ void exact(float x, bool& stay, float& v) const {   // binary64 instructions
-        const double W = (double)wf;
-        const double dp = __dsub_rn((double)x, sgn > 0 ? draw->ds : -draw->ds);
+    // binary64 instructions.  The conversion of W is a volatile asm, and ds
+    // is added or subtracted rather than negated: binary64 operations on the
+    // loop invariants would otherwise be hoisted out of this rare branch and
+    // issued by every warp (the binary64 pipe is 1/64 of binary32 here).
+    __device__ __forceinline__ void exact(float x, bool& stay, float& v) const {
+        double W;
+        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(W) : "f"(wf));
+        const double xd = (double)x, ds = draw->ds;
+        const double dp = sgn > 0 ? __dsub_rn(xd, ds) : __dadd_rn(xd, ds);
         stay = Prm<double>::ge0(dp) && Prm<double>::lt(dp, W);
-        v = __double2float_rn(stay ? dp : __dadd_rn(dp, sgn > 0 ? W : -W));
+        v = __double2float_rn(stay ? dp : (sgn > 0 ? __dadd_rn(dp, W) : __dsub_rn(dp, W)));
     }
     __device__ __forceinline__ void stayer(float x, bool& stay, float& v) const {
         float s, t, sw;
@@ -157,7 +166,7 @@ __device__ __forceinline__ void shift_cells(const Geometry& g, const T* __restri
     const int ax = fdir >> 1;
     const int sgn = (fdir & 1) ? -1 : 1;
     const ShiftParams<T> P(g, *draw, ax, sgn);
-    if (hx == 0 && hy == 0 && q == 0) add_origin(st, ax, P.origin_step());
+    if (hx == 0 && hy == 0 && q == 0) add_origin(st, ax, sgn, P.origin_ds());
     if (hx >= g.hx || hy >= g.hy) return;
     const int cx = 2 * hx + (q & 1), cy = 2 * hy + (q >> 1);
     if (cy < g.slo || cy > g.shi) return;   // a strip's halo rows are not its own
@@ -210,7 +219,11 @@ k_shift(const Geometry g, const T* __restrict__ src, T* __restrict__ dst, const 
         DevState* __restrict__ st) {
     pdl_release();
     pdl_wait();
-    shift_cells<T>(g, src, dst, draw, st, blockIdx.x, blockIdx.y, blockIdx.z);
+    // the four sets of one tile are adjacent blocks (set = blockIdx.x & 3), so
+    // the old cells a block reads from the neighbouring set are read by that
+    // set's block at about the same time: the second read hits L2 even when
+    // the state does not fit there
+    shift_cells<T>(g, src, dst, draw, st, blockIdx.x >> 2, blockIdx.y, blockIdx.x & 3);
 }
 
 // ---- contact histogram: Sec. 4 ------------------------------------------------------
@@ -502,8 +515,7 @@ k_shift_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __rest
     const int r = map[blockIdx.x];
     const ReplicaDesc* rd = reps + r;
     const int local = (int)blockIdx.x - rd->sh_block0;
-    const int per_set = rd->sh_gx * rd->sh_gy;
-    const int q = local / per_set, rem = local - q * per_set;
+    const int q = local & 3, rem = local >> 2;   // the four sets of a tile in adjacent blocks
     const int by = rem / rd->sh_gx, bx = rem - by * rd->sh_gx;
     shift_cells<T>(rd->g, src + 8 * rd->cell_off, dst + 8 * rd->cell_off, draws + (size_t)j * R + r, sts + r, bx,
                    by, q);
@@ -530,7 +542,8 @@ inline dim3 set_grid(const Geometry& g, dim3 block) {
 template <typename T>
 void launch_shift_t(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     const dim3 block(kShiftBX, kShiftBY);
-    launch_on(c, k_shift<T>, set_grid(c.g, block), block, c.g, reinterpret_cast<const T*>(src),
+    const dim3 sg = set_grid(c.g, block);
+    launch_on(c, k_shift<T>, dim3(4 * sg.x, sg.y, 1), block, c.g, reinterpret_cast<const T*>(src),
               reinterpret_cast<T*>(dst), draw, c.st);
 }
 
