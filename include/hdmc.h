@@ -471,8 +471,7 @@ void hdmc_batch_destroy(hdmc_batch_t *b);
  * HDMC_ECUDA.  Synchronises the stream.
  * The first call on each device looks up the device address of the scratch
  * array (with that device current) and keeps it for the life of the
- * process; that first call must not come while a stream is being captured.
- * cudaDeviceReset may move the array, so do not use this entry point in a
+ * process.  cudaDeviceReset may move the array, so do not use this entry point in a
  * process that resets a device it has called it on.  All calls share the
  * array and each call clears it first, so calls that overlap on the GPU
  * (several streams or host threads) race. */
