@@ -85,6 +85,30 @@ def test_snapshot_resume_is_bit_identical_and_matches_oracle(prec):
     assert np.array_equal(b.counters(), o.counters())
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_snapshot_resume_with_crowded_cells(prec):
+    # the paper's cell rule (w just below sqrt(2) sigma) fills cells with up
+    # to four disks; a run resumed from an image of such a state is still
+    # the oracle's straight run
+    from paper_1211_1646_gb300 import hdmc
+    N = 4096
+    L = W.square_box(N, 0.708)
+    a = hdmc.System(N, *L, 1.0, 0.16, 4, 21, prec, cells="sqrt2")
+    a.sweep(30)
+    img = a.save()
+    _, cnt = a.state()
+    assert (cnt >= 3).sum() > 20 and (cnt == 4).sum() > 0
+    b = hdmc.System(N, *L, 1.0, 0.16, 4, 5, prec, cells="sqrt2")
+    b.load(img)
+    _same_run(a, b)
+    b.sweep(30)
+    o = O.System(N, *L, 1.0, 0.16, 4, 21, PREC[prec], cells=O.CELLS_SQRT2)
+    o.sweep(60)
+    assert np.array_equal(b.state()[0], o.state()[0])
+    assert np.array_equal(b.state()[1], o.state()[1])
+    assert np.array_equal(b.counters(), o.counters())
+
+
 def test_snapshot_into_pinned_tensor():
     import torch
     from paper_1211_1646_gb300 import hdmc
