@@ -38,16 +38,22 @@ template <typename T> struct TrialDir;
 template <> struct TrialDir<double> {
     WordStream ws;
     __device__ TrialDir(const G3& g, uint32_t sweep, uint32_t c, uint32_t dom) : ws(g.key0, g.key1, sweep, c, dom) {}
-    __device__ __forceinline__ void next(double& u0, double& u1, double& u2) {
-        uint32_t wd[6];
-        for (;;) {
+    // The next `want` kept directions into column threadIdx.x of u, with the
+    // lanes that still need one drawing their attempts together (from a
+    // common start they stay at the same word of their streams, so the
+    // Philox blocks are computed converged).
+    __device__ __forceinline__ void fill(int want, double (*u)[3][kSubB3]) {
+        for (int have = 0; have < want;) {
+            uint32_t wd[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) wd[q] = ws.next();
-            if (inside_ball(wd)) break;
+            if (inside_ball(wd)) {
+                u[have][0][threadIdx.x] = sym52(wd[0], wd[1]);
+                u[have][1][threadIdx.x] = sym52(wd[2], wd[3]);
+                u[have][2][threadIdx.x] = sym52(wd[4], wd[5]);
+                ++have;
+            }
         }
-        u0 = sym52(wd[0], wd[1]);
-        u1 = sym52(wd[2], wd[3]);
-        u2 = sym52(wd[4], wd[5]);
     }
 };
 template <> struct TrialDir<float> {
@@ -56,22 +62,39 @@ template <> struct TrialDir<float> {
     int triple;
     __device__ TrialDir(const G3& g, uint32_t sweep_, uint32_t c_, uint32_t dom_)
         : k0(g.key0), k1(g.key1), sweep(sweep_), c(c_), dom(dom_), block(0), triple(2) {}
-    __device__ __forceinline__ void next(float& u0, float& u1, float& u2) {
+    // The next `want` kept directions (attempts in stream order: the field
+    // triples (0,1,2) and (3,4,5) of block 0, then of block 1, ...) into
+    // column threadIdx.x of u.  Lanes that still need a direction compute
+    // their next Philox block together, so the generator runs with the warp
+    // converged, not once for every lane that happens to need a block in a
+    // given trial.
+    __device__ __forceinline__ void fill(int want, float (*u)[3][kSubB3]) {
+        int have = 0;
         for (;;) {
-            if (triple == 2) {
-                fields21(philox4x32_10(make_uint4(sweep, c, dom, block), k0, k1), f);
-                ++block;
-                triple = 0;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (triple == a && have < want) {
+                    const float u0 = sym21(f[3 * a]), u1 = sym21(f[3 * a + 1]), u2 = sym21(f[3 * a + 2]);
+                    ++triple;
+                    if (fmaf(u0, u0, fmaf(u1, u1, u2 * u2)) < 1.0f) {
+                        u[have][0][threadIdx.x] = u0;
+                        u[have][1][threadIdx.x] = u1;
+                        u[have][2][threadIdx.x] = u2;
+                        ++have;
+                    }
+                }
             }
-            const bool second = triple == 1;
-            u0 = sym21(second ? f[3] : f[0]);
-            u1 = sym21(second ? f[4] : f[1]);
-            u2 = sym21(second ? f[5] : f[2]);
-            ++triple;
-            if (fmaf(u0, u0, fmaf(u1, u1, u2 * u2)) < 1.0f) return;
+            if (have >= want) break;
+            fields21(philox4x32_10(make_uint4(sweep, c, dom, block), k0, k1), f);
+            ++block;
+            triple = 0;
         }
     }
 };
+
+// Trial directions drawn ahead per thread (shared memory).
+constexpr int kDir3 = 4;
+template <typename T> struct DirBuf { T u[kDir3][3][kSubB3]; };
 
 // Pair test on binary32 copies of the coordinates: 1 overlap, 0 none, 2 too
 // close to contact for binary32 to decide (binary64 only; the copies are
@@ -202,10 +225,11 @@ __device__ __forceinline__ void gather_cell(const G3& g, const T* cells, const T
 // binary32: the neighbour cells of one x-row are loaded together (256-bit
 // loads) before they are scanned; binary64: one cell at a time.
 template <typename T>
-__global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, const Draw3* __restrict__ table,
-                                                 int jd, int k, Dev3* st) {
+__device__ __forceinline__ void sub3_cells(const G3& g, T* __restrict__ cells, const Draw3* __restrict__ table, int jd,
+                                           int k, Dev3* st) {
     using A = Ar3<T>;
     __shared__ Cand<T> cand;
+    __shared__ DirBuf<T> dirs;
     const Draw3& dr = table[jd];
     const int Q = dr.perm[k];
     const unsigned s = blockIdx.x * kSubB3 + threadIdx.x;
@@ -301,7 +325,13 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
             int i = 0;
             for (int t = 0; t < g.nsel; ++t) {
                 T u0, u1, u2;
-                TD.next(u0, u1, u2);
+                {   // drawn ahead, kDir3 at a time
+                    const int tt = t % kDir3;
+                    if (tt == 0) TD.fill(min(kDir3, g.nsel - t), dirs.u);
+                    u0 = dirs.u[tt][0][threadIdx.x];
+                    u1 = dirs.u[tt][1][threadIdx.x];
+                    u2 = dirs.u[tt][2][threadIdx.x];
+                }
                 const T px = A::trial(g, pick8(x, i), u0);
                 const T py = A::trial(g, pick8(y, i), u1);
                 const T pz = A::trial(g, pick8(z, i), u2);
@@ -362,6 +392,19 @@ __global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, co
         atomicAdd(&st->ctr[2], (unsigned long long)cc);
         atomicAdd(&st->ctr[3], (unsigned long long)d);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSubB3) k_sub3(G3 g, T* __restrict__ cells, const Draw3* __restrict__ table, int jd,
+                                                 int k, Dev3* st) {
+    sub3_cells<T>(g, cells, table, jd, k, st);
+}
+// binary32: eight blocks per SM (128 registers; ten blocks at 96 registers
+// spill and measured slower, 46.8 against 41.5 us)
+template <>
+__global__ void __launch_bounds__(kSubB3, 8) k_sub3<float>(G3 g, float* __restrict__ cells,
+                                                            const Draw3* __restrict__ table, int jd, int k, Dev3* st) {
+    sub3_cells<float>(g, cells, table, jd, k, st);
 }
 
 }  // namespace hdmc
