@@ -689,8 +689,10 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             v, nt, sample = oracle_sample()
+            v1, _, sample1 = oracle_sample(seconds_budget=6.0, threads=1)
             line["cpu_baseline"] = {"value": v, "unit": "trial moves/s", "cores": nt, "kind": "oracle",
-                                    "sample": sample}
+                                    "sample": sample,
+                                    "serial": {"value": v1, "unit": "trial moves/s", "cores": 1, "sample": sample1}}
             if line.get("spheres"):
                 v3, nt3, sample3 = oracle_sample_spheres()
                 line["spheres"]["cpu_baseline"] = {"value": v3, "unit": "trial moves/s", "cores": nt3,
