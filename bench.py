@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-replica batch leg")
     ap.add_argument("--no-n4m", action="store_true", help="skip the N=4M legs")
+    ap.add_argument("--no-paper", action="store_true", help="skip the leg on the paper's Table 4 workload")
     ap.add_argument("--no-spheres", action="store_true", help="skip the hard-sphere (3-d) legs")
     ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres", "batch64"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
@@ -307,11 +308,16 @@ def run_hdmc(args, rank, world, dist):
     def one_step(sysm):
         sysm.sweep(SWEEPS_PER_STEP)
         sysm.sample()
-        return sysm.pressure()
+        return sysm.pressure()[0]
 
-    def timed_steps(sysm, steps, warmup, sampler=None):
+    def sweeps_only(sysm):   # the paper's eta: sweeps alone (Sec. 5.1)
+        sysm.sweep(SWEEPS_PER_STEP)
+        return None
+
+    def timed_steps(sysm, steps, warmup, sampler=None, step=None):
+        step = step or one_step
         for _ in range(warmup):
-            one_step(sysm)
+            step(sysm)
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
@@ -325,7 +331,7 @@ def run_hdmc(args, rank, world, dist):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                bp, g0, _, _ = one_step(sysm)
+                bp = step(sysm)
                 e1.record(stream)
                 e1.synchronize()
                 total_ms += e0.elapsed_time(e1)
@@ -381,7 +387,7 @@ def run_hdmc(args, rank, world, dist):
         c0 = int(s32.counters()[0])
         t0 = time.perf_counter()
         s32.load(snap)                        # H2D: the step's input state
-        bp, g0, _, _ = one_step(s32)          # D2H: histogram -> pressure
+        one_step(s32)                         # D2H: histogram -> pressure
         s32.save(snap)                        # D2H: the state after the step
         t1 = time.perf_counter()
         e2e_trials += int(s32.counters()[0]) - c0
@@ -416,6 +422,22 @@ def run_hdmc(args, rank, world, dist):
                 "roofline_hbm_frac": bytes4 / (sub4 / 1e3) / 1e9 / hbm_peak,
                 "shift_roofline_hbm_frac": bytes4_shift / (shift4 / 1e3) / 1e9 / hbm_peak}
             s4.close()
+
+    # ---- the paper's own throughput workload (Sec. 5.1, Table 4): N = 1520^2,
+    # phi = 0.698, cells just below sqrt(2) sigma; eta = trial moves of the
+    # sweeps alone per second, for comparison with the paper's K20 figure ----
+    paper = None
+    if not args.no_paper:
+        wp = workloads.paper_table4()
+        sp = hdmc.System(wp.N, wp.Lx, wp.Ly, 1.0, wp.d, wp.nselect, seed, "fp32", device=dev, cells="sqrt2")
+        tp, msp, _ = timed_steps(sp, args.steps, max(1, args.warmup), step=sweeps_only)
+        msp = max_over_ranks(msp)
+        paper = {"workload": wp.name, "N": wp.N, "phi": wp.phi, "cells": [sp.mx, sp.my], "d": wp.d,
+                 "nselect": wp.nselect, "step": "%d sweeps" % SWEEPS_PER_STEP,
+                 "value": sum_over_ranks(tp) / (msp / 1e3), "unit": "trial moves/s", "ms_per_step": msp / args.steps,
+                 "disk_sweeps_per_s": sum_over_ranks(wp.N * SWEEPS_PER_STEP * args.steps) / (msp / 1e3),
+                 "paper_value": 1.09e9, "paper_hardware": "Tesla K20, FP32, the same workload (Table 4)"}
+        sp.close()
 
     # ---- 64 batched replicas of uneven N and phi in one launch per stage ----
     batch = None
@@ -537,6 +559,7 @@ def run_hdmc(args, rank, world, dist):
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": "replicas x%d" % world},
         "e2e": {"value": e2e_value, "unit": "trial moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "disk_sweeps_per_s": sum_over_ranks(w.N * SWEEPS_PER_STEP * args.steps) / (ms_max / 1e3),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
@@ -562,6 +585,7 @@ def run_hdmc(args, rank, world, dist):
         "speedup_fp32_over_fp64": value / value64 if value64 > 0 else None,
         "batch64": batch,
         "n4m": n4m,
+        "paper_table4": paper,
         "spheres": spheres,
         "pressure_betaP_over_rho_last": press[-1] if press else None,
     }

@@ -79,6 +79,16 @@ def n4m(phi: float, precision: str = "fp32") -> Workload:
     return Workload("n4194304_phi%.3f_hex" % phi, 2048 * 2048, Lx, Ly, 0.08, 4, 1, 20000, precision, phi=phi)
 
 
+def paper_table4(precision: str = "fp32") -> Workload:
+    """The paper's own throughput workload (Sec. 5.1, Table 4): N = 1520^2
+    disks at phi = 0.698 in a square box, cells just below sqrt(2) sigma
+    (the paper's cell rule), d = 0.16 and n_M = 4 (the values Sec. 5 finds
+    best for the autocorrelation time per second)."""
+    Lx, Ly = square_box(1520 * 1520, 0.698)
+    return Workload("n2310400_phi0.698_square_sqrt2cells", 1520 * 1520, Lx, Ly, 0.16, 4, 1, 200, precision,
+                    phi=0.698, extra={"cells": "sqrt2"})
+
+
 def batch64(seed: int = 1, R: int = 64, nmin: int = 4096, nmax: int = 262144,
             phimin: float = 0.60, phimax: float = 0.74):
     """Replica list: N log-uniform in [nmin, nmax] (rounded to a hexagonal
