@@ -58,6 +58,7 @@ struct Geometry {
     int row0;              // global cell row of row 0 (random streams use global cell numbers)
     int ylo, yhi;          // rows whose cells make trial moves
     int slo, shi;          // rows the shift writes and the contact histogram counts
+    int dense;             // cells hold 1.3 disks or more on average (binary32 sub-sweep variant)
 };
 
 // Device error word bits: a cell received more than its slots (bit 0); a

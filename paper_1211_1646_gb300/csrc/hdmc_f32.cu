@@ -7,10 +7,16 @@ void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw,
     // blocks of two set rows of 32 cells: in-step faster than one-row blocks
     // (fewer blocks to schedule) and as fast as four-row blocks
     const dim3 grid((unsigned)((c.g.hx + 31) / 32), (unsigned)((c.g.hy + 1) / 2));
-    if (c.g.nsel == 4)
+    if (c.g.dense) {   // cells that often hold three or four disks
+        if (c.g.nsel == 4)
+            launch_on(c, k_subsweep_f32<2, 4, true>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
+        else
+            launch_on(c, k_subsweep_f32<2, 0, true>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
+    } else if (c.g.nsel == 4) {
         launch_on(c, k_subsweep_f32<2, 4>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
-    else
+    } else {
         launch_on(c, k_subsweep_f32<2, 0>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
+    }
 }
 void launch_shift_f32(const LaunchCtx& c, const void* src, void* dst, const SweepDraw* draw) {
     launch_shift_t<float>(c, src, dst, draw);

@@ -92,6 +92,7 @@ int make_system(SysDesc& d, int64_t N, double Lx, double Ly, double sigma, doubl
     g.row0 = 0;
     g.ylo = g.slo = 0;
     g.yhi = g.shi = my - 1;
+    g.dense = 10 * N >= 13 * g.C;   // 1.3 disks or more per cell on average
     d.N = N;
     d.Lx = Lx;
     d.Ly = Ly;

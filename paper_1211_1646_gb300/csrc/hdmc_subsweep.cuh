@@ -54,7 +54,11 @@ __device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t swee
     }
 }
 
-template <int ROWS, int NSEL, bool TRACK = false>
+// DENSE (cells that often hold three or four disks, as with the paper's
+// cells just below sqrt(2) sigma): slot pairs (2,3) of all 8 neighbours stay
+// in registers and every trial tests all of them, instead of the flagged
+// directions' pairs being read again in every trial.
+template <int ROWS, int NSEL, bool TRACK = false, bool DENSE = false>
 __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restrict__ cells,
                                              const SweepDraw* __restrict__ draw, int k, int bx, int by,
                                              unsigned long long* __restrict__ bpart,
@@ -77,16 +81,19 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     if (live) load_cell(ownp, own);
     float4 n01[8];   // slots 0,1 of the neighbours (x0 x1 y0 y1); slot 2 only to flag its use
     float n2[8];
+    float4 n23[DENSE ? 8 : 1];   // DENSE: slots 2,3 of the neighbours (x2 x3 y2 y3)
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         n01[c] = make_float4((float)kEmpty, (float)kEmpty, (float)kEmpty, (float)kEmpty);
         n2[c] = (float)kEmpty;
+        if (DENSE) n23[c] = n01[c];
         if (live) {
             const float* p = cell_at(cells, nbh.index(g, c, hx, hy));
             Cell<float> a;
             load_cell_ro(p, a);   // one 256-bit load; slots 0, 1 and x2 are used
             n01[c] = make_float4(a.x[0], a.x[1], a.y[0], a.y[1]);
             n2[c] = a.x[2];
+            if (DENSE) n23[c] = make_float4(a.x[2], a.x[3], a.y[2], a.y[3]);
         }
     }
 
@@ -135,17 +142,22 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
             }
         }
         f2x qx01[8], qy01[8];
+        f2x qx23[DENSE ? 8 : 1], qy23[DENSE ? 8 : 1];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float sx = (float)dir_dx(c) * g.wxf, sy = (float)dir_dy(c) * g.wyf;
             qx01[c] = add2(pk(n01[c].x, n01[c].y), pk(sx, sx));
             qy01[c] = add2(pk(n01[c].z, n01[c].w), pk(sy, sy));
+            if (DENSE) {
+                qx23[c] = add2(pk(n23[c].x, n23[c].y), pk(sx, sx));
+                qy23[c] = add2(pk(n23[c].z, n23[c].w), pk(sy, sy));
+            }
         }
         // slot pair (2,3) of the first flagged direction, translated; further
         // flagged directions (rare) are read in the trial loop
         f2x fx23 = 0, fy23 = 0;
-        const uint32_t more23 = dir23 & (dir23 - 1);
-        if (dir23) {
+        const uint32_t more23 = DENSE ? 0u : dir23 & (dir23 - 1);
+        if (!DENSE && dir23) {
             const int c = __ffs(dir23) - 1;
             const float2* p = reinterpret_cast<const float2*>(cell_at(cells, nbh.index(g, c, hx, hy)));
             const float2 x23 = __ldg(p + 1), y23 = __ldg(p + 3);
@@ -174,7 +186,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 // own cell: every other occupied slot (slot i excluded)
                 f2x z = zpair(tx2, ty2, pk(own.x[0], own.x[1]), pk(own.y[0], own.y[1]), ns2);
                 uint32_t acc = ((M & 1u) && i == 0 ? 0u : lo32(z)) | ((M & 2u) && i == 1 ? 0u : hi32(z));
-                if (own23) {
+                if (DENSE || own23) {
                     z = zpair(tx2, ty2, pk(own.x[2], own.x[3]), pk(own.y[2], own.y[3]), ns2);
                     acc |= ((M & 4u) && i == 2 ? 0u : lo32(z)) | ((M & 8u) && i == 3 ? 0u : hi32(z));
                 }
@@ -182,8 +194,12 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
                 for (int c = 0; c < 8; ++c) {
                     z = zpair(tx2, ty2, qx01[c], qy01[c], ns2);
                     acc |= lo32(z) | hi32(z);
+                    if (DENSE) {
+                        z = zpair(tx2, ty2, qx23[c], qy23[c], ns2);
+                        acc |= lo32(z) | hi32(z);
+                    }
                 }
-                if (dir23) {
+                if (!DENSE && dir23) {
                     z = zpair(tx2, ty2, fx23, fy23, ns2);
                     acc |= lo32(z) | hi32(z);
                 }
@@ -231,8 +247,8 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     add_block_counters<ROWS>(n_tr, n_acc, n_leave, bpart);
 }
 
-template <int ROWS, int NSEL>
-static __global__ void __launch_bounds__(32 * ROWS, 20 / ROWS)
+template <int ROWS, int NSEL, bool DENSE = false>
+static __global__ void __launch_bounds__(32 * ROWS, DENSE ? 16 / ROWS : 20 / ROWS)
 k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __restrict__ draw, int k,
                unsigned long long* __restrict__ partial) {
     pdl_release();
@@ -241,7 +257,7 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
     // counters of the tile that holds this block (shared by the blocks of a
     // tile: atomic adds)
     const long long slot = (long long)(blockIdx.y * ROWS / kCounterRows) * gridDim.x + blockIdx.x;
-    subsweep_f32<ROWS, NSEL>(g, cells, draw, k, blockIdx.x, blockIdx.y, partial + 4 * slot, sdir);
+    subsweep_f32<ROWS, NSEL, false, DENSE>(g, cells, draw, k, blockIdx.x, blockIdx.y, partial + 4 * slot, sdir);
 }
 
 // ---- binary64 sub-sweep ---------------------------------------------------------------
