@@ -115,6 +115,8 @@ struct hdmc_batch_handle {
         c.hi_blocks = lay.hi_blocks;
         c.R = R;
         c.rows = rows;
+        c.dense = true;
+        for (const SysDesc& d : sys) c.dense = c.dense && d.g.dense;
         c.sts = sts;
         c.partial = partial;
         c.hist = hist;

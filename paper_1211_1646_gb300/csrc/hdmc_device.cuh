@@ -282,6 +282,7 @@ struct BatchCtx {
     int sub_blocks, sh_blocks, hi_blocks;
     int R;
     int rows;                      // sub-sweep block height (binary32): 2, 4 or 8
+    bool dense;                    // every replica has crowded cells (Geometry::dense): dense binary32 kernel
     DevState* sts;
     unsigned long long* partial;
     unsigned long long* hist;      // R x kHistBins

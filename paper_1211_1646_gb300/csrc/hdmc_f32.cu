@@ -35,13 +35,22 @@ void launch_check_f32(const LaunchCtx& c, const void* cells, unsigned long long*
 
 void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k, bool track) {
     float* a = reinterpret_cast<float*>(arena);
-#define HDMC_SUB_BATCH(ROWS, TRACK)                                                                        \
-    k_subsweep_f32_batch<ROWS, TRACK><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(c.reps, c.sub_map, a, draws, \
-                                                                                      c.R, j, k, c.partial, c.msd)
-    if (c.rows == 1) { if (track) HDMC_SUB_BATCH(1, true); else HDMC_SUB_BATCH(1, false); }
-    else if (c.rows == 2) { if (track) HDMC_SUB_BATCH(2, true); else HDMC_SUB_BATCH(2, false); }
-    else if (c.rows == 8) { if (track) HDMC_SUB_BATCH(8, true); else HDMC_SUB_BATCH(8, false); }
-    else { if (track) HDMC_SUB_BATCH(4, true); else HDMC_SUB_BATCH(4, false); }
+#define HDMC_SUB_BATCH(ROWS, TRACK, DENSE)                                                                 \
+    k_subsweep_f32_batch<ROWS, TRACK, DENSE><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(              \
+        c.reps, c.sub_map, a, draws, c.R, j, k, c.partial, c.msd)
+    // crowded cells in every replica: the dense kernel (the autotuner's
+    // tracking launches keep the regular one)
+#define HDMC_SUB_BATCH_ROWS(ROWS)                                                                          \
+    do {                                                                                                   \
+        if (track) HDMC_SUB_BATCH(ROWS, true, false);                                                      \
+        else if (c.dense) HDMC_SUB_BATCH(ROWS, false, true);                                               \
+        else HDMC_SUB_BATCH(ROWS, false, false);                                                           \
+    } while (0)
+    if (c.rows == 1) HDMC_SUB_BATCH_ROWS(1);
+    else if (c.rows == 2) HDMC_SUB_BATCH_ROWS(2);
+    else if (c.rows == 8) HDMC_SUB_BATCH_ROWS(8);
+    else HDMC_SUB_BATCH_ROWS(4);
+#undef HDMC_SUB_BATCH_ROWS
 #undef HDMC_SUB_BATCH
 }
 
