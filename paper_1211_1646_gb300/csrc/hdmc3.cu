@@ -180,13 +180,45 @@ __device__ __noinline__ void hist_pair_exact(T ax, T ay, T az, T qx, T qy, T qz,
     hist_bin((e0 * e0 + e1 * e1) + e2 * e2, edges2, sh);
 }
 
+// Binary32 bounds that decide a pair's bin without binary64 arithmetic.  The
+// binary32 estimate r2f (coordinates rounded to binary32, differences and
+// squares in binary32) lies within kBinMargin sigma^2 of the binary64 r^2
+// the bins are defined on: per axis the estimate's difference is off by at
+// most 7 units of 2^-24 sigma-scaled (|q + d w| <= 3.5 sigma, |p - q - d w|
+// <= 1.03 sigma in the histogram's range, the two roundings of a binary64
+// coordinate), hence r^2 by at most 2 sqrt(3) 1.03 (4.2e-7) + 3 (1.04) 2^-24
+// < 1.7e-6 sigma^2; the margin is 4e-6 sigma^2.  B[2b], B[2b+1] (b < 200):
+// r2f in [B[2b], B[2b+1]) puts the pair in bin b for certain; B[400]: r2f
+// below it is below every bin; B[401]: r2f at or above it is above them.
+constexpr double kBinMargin = 4.0e-6;
+static float float_up(double x) {
+    float f = (float)x;
+    return (double)f < x ? std::nextafter(f, HUGE_VALF) : f;
+}
+static float float_down(double x) {
+    float f = (float)x;
+    return (double)f > x ? std::nextafter(f, -HUGE_VALF) : f;
+}
+static void certified_bins(double sigma, const double* E, float* B) {
+    const double m = kBinMargin * sigma * sigma;
+    for (int b = 0; b < kHistBins; ++b) {
+        B[2 * b] = float_up(E[b] + m);
+        B[2 * b + 1] = float_down(E[b + 1] - m);
+    }
+    B[2 * kHistBins] = float_down(E[0] - m);
+    B[2 * kHistBins + 1] = float_up(E[kHistBins] + m);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict__ cells,
-                                                   const double* __restrict__ edges2, float lo2f, float hi2f,
-                                                   unsigned long long* hist) {
+                                                   const double* __restrict__ edges2, const float* __restrict__ binf,
+                                                   float lo2f, float hi2f, unsigned long long* hist) {
     __shared__ unsigned int sh[kHistBins];
+    __shared__ float sb[2 * kHistBins + 2];
     for (int b = threadIdx.x; b < kHistBins; b += kHistB3) sh[b] = 0;
+    for (int b = threadIdx.x; b < 2 * kHistBins + 2; b += kHistB3) sb[b] = binf[b];
     __syncthreads();
+    const float sigf = (float)g.sigma, inv_drf = (float)(1.0 / (kHistDr * g.sigma));
     const unsigned s = blockIdx.x * kHistB3 + threadIdx.x;
     if (s < g.C) {
         const unsigned Q = s / g.cq, r0 = s % g.cq;
@@ -243,6 +275,14 @@ __global__ void __launch_bounds__(kHistB3, 4) k_hist3(G3 g, const T* __restrict_
                                 const float fx = (float)ax - ex, fy = (float)ay - ey, fz = (float)az - ez;
                                 const float r2f = fx * fx + fy * fy + fz * fz;
                                 if (r2f < lo2f || r2f > hi2f) continue;
+                                // the bin, decided in binary32 where that is certain
+                                int bb = (int)((r2f * rsqrtf(r2f) - sigf) * inv_drf);
+                                bb = bb < 0 ? 0 : (bb > kHistBins - 1 ? kHistBins - 1 : bb);
+                                if (r2f >= sb[2 * bb] && r2f < sb[2 * bb + 1]) {
+                                    atomicAdd(&sh[bb], 1u);
+                                    continue;
+                                }
+                                if (r2f < sb[2 * kHistBins] || r2f >= sb[2 * kHistBins + 1]) continue;
                                 hist_pair_exact<T>(ax, ay, az, qx[j], qy[j], qz[j], dx, dy, dz, w0, w1, w2, edges2, sh);
                             }
                         }
@@ -303,6 +343,7 @@ struct hdmc3_handle {
     Dev3* st;
     unsigned long long* hist;  // kHistBins accumulator
     double* edges2;            // kHistBins + 1 squared bin edges
+    float* binf;               // binary32 bin bounds that decide a bin for certain (certified_bins)
     float lo2f, hi2f;
     int64_t samples;
     uint64_t sweeps, shifts;
@@ -524,6 +565,7 @@ void free3(hdmc3_t* h) {
     cudaFree(h->st);
     cudaFree(h->hist);
     cudaFree(h->edges2);
+    cudaFree(h->binf);
     delete h;
 }
 
@@ -798,12 +840,16 @@ int hdmc3_create(hdmc3_t** out, int64_t N, double Lx, double Ly, double Lz, doub
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->st, sizeof(Dev3));
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->hist, sizeof(unsigned long long) * kHistBins);
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->edges2, sizeof(double) * (kHistBins + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&h->binf, sizeof(float) * (2 * kHistBins + 2));
     if (ce == cudaSuccess) ce = cudaMemcpy(h->cells[0], raw.data(), bytes, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(h->st, 0, sizeof(Dev3));
     if (ce == cudaSuccess) ce = cudaMemset(h->hist, 0, sizeof(unsigned long long) * kHistBins);
     double E[kHistBins + 1];
     squared_edges(sigma, E);
     if (ce == cudaSuccess) ce = cudaMemcpy(h->edges2, E, sizeof(E), cudaMemcpyHostToDevice);
+    float B[2 * kHistBins + 2];
+    certified_bins(sigma, E, B);
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->binf, B, sizeof(B), cudaMemcpyHostToDevice);
     // the set-up above ran on the legacy default stream: finish it before
     // work is enqueued on the handle's stream, which need not wait for it
     if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
@@ -901,10 +947,10 @@ int hdmc3_sample(hdmc3_t* h) {
     const unsigned blocks = (h->g.C + kHistB3 - 1) / kHistB3;
     if (h->prec == HDMC_FP64)
         k_hist3<double><<<blocks, kHistB3, 0, h->stream>>>(h->g, (const double*)h->cells[h->cur], h->edges2,
-                                                            h->lo2f, h->hi2f, h->hist);
+                                                            h->binf, h->lo2f, h->hi2f, h->hist);
     else
         k_hist3<float><<<blocks, kHistB3, 0, h->stream>>>(h->g, (const float*)h->cells[h->cur], h->edges2,
-                                                           h->lo2f, h->hi2f, h->hist);
+                                                           h->binf, h->lo2f, h->hi2f, h->hist);
     h->samples += 1;
     return cuda_code(cudaGetLastError());
 }
