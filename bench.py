@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-n4m", action="store_true", help="skip the N=4M legs")
     ap.add_argument("--no-paper", action="store_true", help="skip the leg on the paper's Table 4 workload")
     ap.add_argument("--no-spheres", action="store_true", help="skip the hard-sphere (3-d) legs")
-    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres", "batch64"],
+    ap.add_argument("--ncu-case", default=None, choices=["n1m", "n4m", "spheres", "batch64", "table4"],
                     help="run a short fixed workload for an ncu capture and exit (no timing)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     return ap.parse_args()
@@ -58,7 +58,8 @@ def parse():
 
 def ncu_case(args):
     """A few sweeps and one contact histogram of the N=1M (74 MB of binary32
-    state) or N=4M (294 MB, larger than L2) phi=0.716 workload."""
+    state) or N=4M (294 MB, larger than L2) phi=0.716 workload, of the
+    paper's Table 4 workload, of the 64-replica batch or of the spheres."""
     import torch
     from paper_1211_1646_gb300 import build, hdmc, workloads
     build.build()
@@ -81,8 +82,12 @@ def ncu_case(args):
         torch.cuda.synchronize()
         print("ncu case %s %s done: counters %s" % (w.name, args.precision, list(s.counters())))
         return
-    w = workloads.n1m_phi0716() if args.ncu_case == "n1m" else workloads.n4m(0.716)
-    s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, args.precision)
+    if args.ncu_case == "table4":
+        w = workloads.paper_table4()
+        s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, args.precision, cells="sqrt2")
+    else:
+        w = workloads.n1m_phi0716() if args.ncu_case == "n1m" else workloads.n4m(0.716)
+        s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, 1, args.precision)
     s.sweep(3)
     s.sample()
     s.pressure()
