@@ -117,6 +117,32 @@ def test_batch_paper_cell_rule(prec):
         assert np.array_equal(b.counters()[r], o.counters())
 
 
+@pytest.mark.parametrize("rows", [1, 8])
+def test_batch_crowded_cells(rows):
+    # every replica with cells of 1.3 disks or more on average (Sec. 3.1
+    # cells, phi >= 0.62): the batch runs the binary32 crowded-cell
+    # sub-sweep, here with four different n_M, bit for bit with the oracle
+    from paper_1211_1646_gb300 import hdmc
+    reps = []
+    for i, (nx, ny, phi, nsel) in enumerate([(40, 36, 0.62, 1), (33, 50, 0.68, 2), (64, 64, 0.72, 8),
+                                             (27, 22, 0.74, 3)]):
+        Lx, Ly = W.hex_box(nx, ny, phi)
+        reps.append(W.Workload("crowded%d" % i, nx * ny, Lx, Ly, 0.12, nsel, 41 + i, 0))
+    b = hdmc.Batch(reps, precision="fp32", cells="sqrt2")
+    b.set_rows(rows)
+    orcs = [O.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, w.seed, O.FP32, cells=O.CELLS_SQRT2) for w in reps]
+    for r, (w, o) in enumerate(zip(reps, orcs)):
+        assert (b.grids[r]["mx"], b.grids[r]["my"]) == (o.mx, o.my)
+        assert 10 * w.N >= 13 * o.mx * o.my   # the library's crowded-cell rule
+    b.sweep(12)
+    for o in orcs:
+        o.sweep(12)
+    for r, o in enumerate(orcs):
+        assert np.array_equal(b.state(r)[1], o.state()[1])
+        assert np.array_equal(b.state(r)[0], o.state()[0])
+        assert np.array_equal(b.counters()[r], o.counters())
+
+
 def test_batch_autotune_and_invariants():
     from scipy.spatial import cKDTree
     from paper_1211_1646_gb300 import hdmc

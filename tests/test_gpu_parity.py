@@ -254,6 +254,28 @@ def test_paper_cell_rule(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nsel", [1, 7])
+def test_crowded_cells_any_nselect(prec, nsel):
+    # Cells holding 1.3 disks or more on average (the Sec. 3.1 cells at
+    # phi = 0.708) select the binary32 sub-sweep variant that keeps every
+    # neighbour slot in registers; an n_M other than 4 runs its trial loop in
+    # chunks of drawn directions.  A hexagonal box whose half grid (61 x 34
+    # cells per set) leaves ragged blocks in both directions.
+    from paper_1211_1646_gb300 import hdmc
+    nx, ny = 150, 98
+    Lx, Ly = W.hex_box(nx, ny, 0.708)
+    N = nx * ny
+    g = hdmc.System(N, Lx, Ly, 1.0, 0.12, nsel, 31, prec, cells="sqrt2")
+    r = O.System(N, Lx, Ly, 1.0, 0.12, nsel, 31, PREC[prec], cells=O.CELLS_SQRT2)
+    assert (g.mx, g.my) == (r.mx, r.my) == (122, 68)
+    assert 10 * N >= 13 * g.mx * g.my   # the crowded-cell rule of the library
+    _same(g, r, "start")
+    g.sweep(10)
+    r.sweep(10)
+    _same(g, r, "after 10 sweeps")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_contact_histogram_and_pressure(prec):
     w = W.n65536_phi070()
     g, r = _pair(w, prec)
