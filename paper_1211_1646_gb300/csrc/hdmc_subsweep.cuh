@@ -54,6 +54,45 @@ __device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t swee
     }
 }
 
+// All WANT <= kDirChunk - 2 directions of a cell update in one pass, in the
+// stream order of draw_directions: the two attempts of block 0 (field pairs
+// 1 and 2), blocks 1 and 2 without a loop (every lane needs block 1 and
+// nearly every warp has a lane that needs block 2), then block after block
+// while the lane has fewer than WANT kept attempts.  A lane may keep more
+// than WANT (at most 8 = kDirChunk), in rows of sdir that no trial reads;
+// the stream is not continued.
+template <int ROWS, int WANT>
+__device__ __forceinline__ void draw_directions_once(const Geometry& g, uint32_t sweep, uint32_t cell, uint32_t c2,
+                                                     const uint32_t F0[6], float2 (*__restrict__ sdir)[32 * ROWS],
+                                                     int tid) {
+    static_assert(WANT + 2 <= kDirChunk && kDirChunk >= 8, "sdir holds the extra kept attempts");
+    int have = 0;
+    auto attempt = [&](uint32_t a, uint32_t b) {
+        const float u = sym21(a), v = sym21(b);
+        if (__fmaf_rn(u, u, __fmul_rn(v, v)) < 1.0f) {
+            sdir[have][tid] = make_float2(u, v);
+            ++have;
+        }
+    };
+    attempt(F0[2], F0[3]);
+    attempt(F0[4], F0[5]);
+#pragma unroll
+    for (uint32_t blk = 1; blk < 3; ++blk) {   // every lane needs block 1, nearly every warp block 2
+        uint32_t F[6];
+        fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+        attempt(F[0], F[1]);
+        attempt(F[2], F[3]);
+        attempt(F[4], F[5]);
+    }
+    for (uint32_t blk = 3; have < WANT; ++blk) {
+        uint32_t F[6];
+        fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+        attempt(F[0], F[1]);
+        attempt(F[2], F[3]);
+        attempt(F[4], F[5]);
+    }
+}
+
 // DENSE (cells that often hold three or four disks, as with the paper's
 // cells just below sqrt(2) sigma): slot pairs (2,3) of all 8 neighbours stay
 // in registers and every trial tests all of them, instead of the flagged
@@ -105,7 +144,10 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const uint32_t f0 = F[0];   // shuffle draw
     uint32_t blk = 0;
     int pnext = 1;               // next attempt: field pair 1 of block 0 (fields 2,3)
-    draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);
+    if constexpr (NSEL > 0 && NSEL + 2 <= kDirChunk)
+        draw_directions_once<ROWS, NSEL>(g, sweep, cell, c2, F, sdir, tid);
+    else
+        draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);
 
     // 3. cell contents
     const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
