@@ -117,6 +117,8 @@ struct hdmc_batch_handle {
         c.rows = rows;
         c.dense = true;
         for (const SysDesc& d : sys) c.dense = c.dense && d.g.dense;
+        c.nsel = sys.empty() ? 0 : sys[0].g.nsel;
+        for (const SysDesc& d : sys) c.nsel = d.g.nsel == c.nsel ? c.nsel : 0;
         c.sts = sts;
         c.partial = partial;
         c.hist = hist;
@@ -484,7 +486,8 @@ int hdmc_batch_set_nselect(hdmc_batch_t* b, const int32_t* nselect) {
     int e = cuda_code(cudaStreamSynchronize(b->stream));
     if (e) return e;
     for (int r = 0; r < b->R; ++r) b->sys[r].g.nsel = nselect[r];
-    return upload_layout(b, b->rows);   // descriptors are read at run time: recorded graphs stay valid
+    b->drop_graphs();   // the sub-sweep kernel depends on whether all replicas share one n_M
+    return upload_layout(b, b->rows);
 }
 
 int hdmc_batch_set_balance(hdmc_batch_t* b, const int32_t* shuffle_particles, const int32_t* shuffle_sets) {

@@ -23,6 +23,7 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 constexpr int kDirChunk = 8;   // trial directions drawn ahead per thread (binary32 sub-sweep)
+constexpr int kDirRows = kDirChunk + 2;   // rows of its buffer: a one-pass draw keeps up to two more
 
 // ---- packed binary32 pairs (Blackwell f32x2 arithmetic, IEEE round-to-nearest per lane) ----
 typedef unsigned long long f2x;

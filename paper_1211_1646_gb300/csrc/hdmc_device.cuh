@@ -283,6 +283,7 @@ struct BatchCtx {
     int R;
     int rows;                      // sub-sweep block height (binary32): 2, 4 or 8
     bool dense;                    // every replica has crowded cells (Geometry::dense): dense binary32 kernel
+    int nsel;                      // n_M of every replica, or 0 if they differ
     DevState* sts;
     unsigned long long* partial;
     unsigned long long* hist;      // R x kHistBins

@@ -10,10 +10,14 @@ void launch_subsweep_f32(const LaunchCtx& c, void* cells, const SweepDraw* draw,
     if (c.g.dense) {   // cells that often hold three or four disks
         if (c.g.nsel == 4)
             launch_on(c, k_subsweep_f32<2, 4, true>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
+        else if (c.g.nsel == 8)
+            launch_on(c, k_subsweep_f32<2, 8, true>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
         else
             launch_on(c, k_subsweep_f32<2, 0, true>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
     } else if (c.g.nsel == 4) {
         launch_on(c, k_subsweep_f32<2, 4>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
+    } else if (c.g.nsel == 8) {
+        launch_on(c, k_subsweep_f32<2, 8>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
     } else {
         launch_on(c, k_subsweep_f32<2, 0>, grid, dim3(32, 2), c.g, a, draw, k, c.partial);
     }
@@ -35,22 +39,30 @@ void launch_check_f32(const LaunchCtx& c, const void* cells, unsigned long long*
 
 void launch_subsweep_f32_batch(const BatchCtx& c, void* arena, const SweepDraw* draws, int j, int k, bool track) {
     float* a = reinterpret_cast<float*>(arena);
-#define HDMC_SUB_BATCH(ROWS, TRACK, DENSE)                                                                 \
-    k_subsweep_f32_batch<ROWS, TRACK, DENSE><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(              \
+#define HDMC_SUB_BATCH(ROWS, TRACK, DENSE, NSEL)                                                           \
+    k_subsweep_f32_batch<ROWS, TRACK, DENSE, NSEL><<<c.sub_blocks, dim3(32, ROWS), 0, c.stream>>>(        \
         c.reps, c.sub_map, a, draws, c.R, j, k, c.partial, c.msd)
-    // crowded cells in every replica: the dense kernel (the autotuner's
-    // tracking launches keep the regular one)
+    // crowded cells in every replica: the dense kernel; one n_M shared by
+    // every replica (4 or 8): the kernel with n_M fixed (the autotuner's
+    // tracking launches keep the general one)
+#define HDMC_SUB_BATCH_NSEL(ROWS, DENSE)                                                                   \
+    do {                                                                                                   \
+        if (c.nsel == 4) HDMC_SUB_BATCH(ROWS, false, DENSE, 4);                                            \
+        else if (c.nsel == 8) HDMC_SUB_BATCH(ROWS, false, DENSE, 8);                                       \
+        else HDMC_SUB_BATCH(ROWS, false, DENSE, 0);                                                        \
+    } while (0)
 #define HDMC_SUB_BATCH_ROWS(ROWS)                                                                          \
     do {                                                                                                   \
-        if (track) HDMC_SUB_BATCH(ROWS, true, false);                                                      \
-        else if (c.dense) HDMC_SUB_BATCH(ROWS, false, true);                                               \
-        else HDMC_SUB_BATCH(ROWS, false, false);                                                           \
+        if (track) HDMC_SUB_BATCH(ROWS, true, false, 0);                                                   \
+        else if (c.dense) HDMC_SUB_BATCH_NSEL(ROWS, true);                                                 \
+        else HDMC_SUB_BATCH_NSEL(ROWS, false);                                                             \
     } while (0)
     if (c.rows == 1) HDMC_SUB_BATCH_ROWS(1);
     else if (c.rows == 2) HDMC_SUB_BATCH_ROWS(2);
     else if (c.rows == 8) HDMC_SUB_BATCH_ROWS(8);
     else HDMC_SUB_BATCH_ROWS(4);
 #undef HDMC_SUB_BATCH_ROWS
+#undef HDMC_SUB_BATCH_NSEL
 #undef HDMC_SUB_BATCH
 }
 

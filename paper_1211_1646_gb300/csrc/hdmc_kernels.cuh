@@ -481,17 +481,18 @@ k_psi6(const Geometry g, const T* __restrict__ cells, double rc2, double* __rest
 // each replica keeps its own geometry, cells, draws, device state,
 // counters and histogram.  Replica r's cells start at cell rd.cell_off of
 // the arena; its sweep draws of chunk position j sit at draws[j*R + r].
-template <int ROWS, bool TRACK, bool DENSE = false>
+// NSEL > 0: every replica makes NSEL trial moves per cell update.
+template <int ROWS, bool TRACK, bool DENSE = false, int NSEL = 0>
 static __global__ void __launch_bounds__(32 * ROWS, DENSE ? (16 / ROWS > 0 ? 16 / ROWS : 1) : 20 / ROWS)
 k_subsweep_f32_batch(const ReplicaDesc* __restrict__ reps, const unsigned short* __restrict__ map,
                      float* __restrict__ arena, const SweepDraw* __restrict__ draws, int R, int j, int k,
                      unsigned long long* __restrict__ partial, double* __restrict__ msd) {
-    __shared__ float2 sdir[kDirChunk][32 * ROWS];
+    __shared__ float2 sdir[kDirRows][32 * ROWS];
     const int r = map[blockIdx.x];
     const ReplicaDesc* rd = reps + r;
     const int local = (int)blockIdx.x - rd->sub_block0;
     const int by = local / rd->sub_gx, bx = local - by * rd->sub_gx;
-    subsweep_f32<ROWS, 0, TRACK, DENSE>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
+    subsweep_f32<ROWS, NSEL, TRACK, DENSE>(rd->g, arena + 8 * rd->cell_off, draws + (size_t)j * R + r, k, bx, by,
                                      partial + 4 * (rd->part_off + local), sdir, msd + r);
 }
 

@@ -54,18 +54,18 @@ __device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t swee
     }
 }
 
-// All WANT <= kDirChunk - 2 directions of a cell update in one pass, in the
+// All WANT <= kDirChunk directions of a cell update in one pass, in the
 // stream order of draw_directions: the two attempts of block 0 (field pairs
 // 1 and 2), blocks 1 and 2 without a loop (every lane needs block 1 and
 // nearly every warp has a lane that needs block 2), then block after block
 // while the lane has fewer than WANT kept attempts.  A lane may keep more
-// than WANT (at most 8 = kDirChunk), in rows of sdir that no trial reads;
-// the stream is not continued.
+// than WANT (at most max(8, WANT + 2) <= kDirRows), in rows of sdir that no
+// trial reads; the stream is not continued.
 template <int ROWS, int WANT>
 __device__ __forceinline__ void draw_directions_once(const Geometry& g, uint32_t sweep, uint32_t cell, uint32_t c2,
                                                      const uint32_t F0[6], float2 (*__restrict__ sdir)[32 * ROWS],
                                                      int tid) {
-    static_assert(WANT + 2 <= kDirChunk && kDirChunk >= 8, "sdir holds the extra kept attempts");
+    static_assert(WANT <= kDirChunk && kDirRows >= kDirChunk + 2 && kDirRows >= 8, "sdir rows");
     int have = 0;
     auto attempt = [&](uint32_t a, uint32_t b) {
         const float u = sym21(a), v = sym21(b);
@@ -144,7 +144,7 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const uint32_t f0 = F[0];   // shuffle draw
     uint32_t blk = 0;
     int pnext = 1;               // next attempt: field pair 1 of block 0 (fields 2,3)
-    if constexpr (NSEL > 0 && NSEL + 2 <= kDirChunk)
+    if constexpr (NSEL > 0 && NSEL <= kDirChunk)
         draw_directions_once<ROWS, NSEL>(g, sweep, cell, c2, F, sdir, tid);
     else
         draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);
@@ -295,7 +295,7 @@ k_subsweep_f32(const Geometry g, float* __restrict__ cells, const SweepDraw* __r
                unsigned long long* __restrict__ partial) {
     pdl_release();
     pdl_wait();
-    __shared__ float2 sdir[kDirChunk][32 * ROWS];
+    __shared__ float2 sdir[kDirRows][32 * ROWS];
     // counters of the tile that holds this block (shared by the blocks of a
     // tile: atomic adds)
     const long long slot = (long long)(blockIdx.y * ROWS / kCounterRows) * gridDim.x + blockIdx.x;

@@ -117,17 +117,18 @@ def test_batch_paper_cell_rule(prec):
         assert np.array_equal(b.counters()[r], o.counters())
 
 
-@pytest.mark.parametrize("rows", [1, 8])
-def test_batch_crowded_cells(rows):
+@pytest.mark.parametrize("rows,common", [(1, None), (8, None), (2, 4), (4, 8)])
+def test_batch_crowded_cells(rows, common):
     # every replica with cells of 1.3 disks or more on average (Sec. 3.1
     # cells, phi >= 0.62): the batch runs the binary32 crowded-cell
-    # sub-sweep, here with four different n_M, bit for bit with the oracle
+    # sub-sweep, with four different n_M or one n_M shared by every replica
+    # (4 or 8: a kernel with n_M fixed), bit for bit with the oracle
     from paper_1211_1646_gb300 import hdmc
     reps = []
     for i, (nx, ny, phi, nsel) in enumerate([(40, 36, 0.62, 1), (33, 50, 0.68, 2), (64, 64, 0.72, 8),
                                              (27, 22, 0.74, 3)]):
         Lx, Ly = W.hex_box(nx, ny, phi)
-        reps.append(W.Workload("crowded%d" % i, nx * ny, Lx, Ly, 0.12, nsel, 41 + i, 0))
+        reps.append(W.Workload("crowded%d" % i, nx * ny, Lx, Ly, 0.12, common or nsel, 41 + i, 0))
     b = hdmc.Batch(reps, precision="fp32", cells="sqrt2")
     b.set_rows(rows)
     orcs = [O.System(w.N, w.Lx, w.Ly, 1.0, w.d, w.nselect, w.seed, O.FP32, cells=O.CELLS_SQRT2) for w in reps]
@@ -141,6 +142,34 @@ def test_batch_crowded_cells(rows):
         assert np.array_equal(b.state(r)[1], o.state()[1])
         assert np.array_equal(b.state(r)[0], o.state()[0])
         assert np.array_equal(b.counters()[r], o.counters())
+
+
+@pytest.mark.parametrize("common", [4, 8])
+def test_batch_common_nselect(common):
+    # One n_M shared by every replica selects a binary32 kernel with n_M
+    # fixed.  The batch changes n_M between runs (shared, differing, shared
+    # again); each replica must follow a chain of single systems running the
+    # same phases (one per phase, started from the state the previous one
+    # ended in).
+    from paper_1211_1646_gb300 import hdmc
+    reps = [W.Workload(w.name, w.N, w.Lx, w.Ly, w.d, common, w.seed, 0) for w in _replicas()]
+    b = hdmc.Batch(reps, precision="fp32")
+    states = [None] * len(reps)
+    for ns in ([common] * 4, [common, 3, common, 1], [common] * 4):
+        b.set_nselect(ns)
+        b.sweep(9)
+        for r, (w, m) in enumerate(zip(reps, ns)):
+            s = hdmc.System(w.N, w.Lx, w.Ly, 1.0, w.d, m, w.seed, "fp32")
+            if states[r] is not None:
+                s.set_state(*states[r])
+            s.sweep(9)
+            loc, cnt = s.state()
+            info = s.info()
+            states[r] = (loc, cnt, info["origin"], info["sweeps_done"], info["shifts_done"])
+            lb, cb = b.state(r)
+            assert np.array_equal(cb, cnt), "n_M %s, replica %d counts" % (ns, r)
+            assert np.array_equal(lb, loc), "n_M %s, replica %d positions" % (ns, r)
+            assert np.array_equal(b.origin(r), info["origin"]), "n_M %s, replica %d origin" % (ns, r)
 
 
 def test_batch_autotune_and_invariants():

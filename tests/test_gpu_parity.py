@@ -254,7 +254,7 @@ def test_paper_cell_rule(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("nsel", [1, 7])
+@pytest.mark.parametrize("nsel", [1, 7, 8])
 def test_crowded_cells_any_nselect(prec, nsel):
     # Cells holding 1.3 disks or more on average (the Sec. 3.1 cells at
     # phi = 0.708) select the binary32 sub-sweep variant that keeps every
@@ -386,9 +386,11 @@ def test_invariants_on_gpu_fp32_long_run():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("nsel", [1, 12, 20])
+@pytest.mark.parametrize("nsel", [1, 8, 12, 20])
 def test_trials_per_cell(prec, nsel):
-    # n_M = 1 and n_M above the 8 directions drawn ahead per block of work
+    # n_M = 1, n_M = 8 (a binary32 kernel with n_M fixed, its directions
+    # drawn in one pass) and n_M above the 8 directions drawn ahead per
+    # block of work
     w = W.n1024_phi070()
     g, r = _pair(w, prec, nsel=nsel, seed=4)
     g.sweep(25)
