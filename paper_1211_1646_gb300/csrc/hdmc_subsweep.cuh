@@ -54,6 +54,43 @@ __device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t swee
     }
 }
 
+// Philox4x32-10 (the library's philox4x32_10, the same function) with the
+// round keys of one key computed once per thread.  WIDE forms each round's
+// two products as 32 x 32 -> 64-bit multiplies, otherwise as separate high
+// and low products (measured: the wide form is faster in the n_M = 8
+// kernels, the separate one in the n_M = 4 kernels).
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+    __device__ __forceinline__ PhiloxKeys(uint32_t a, uint32_t b) {
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            k0[r] = a + (uint32_t)r * 0x9E3779B9u;
+            k1[r] = b + (uint32_t)r * 0xBB67AE85u;
+        }
+    }
+};
+template <bool WIDE>
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0, lo0, hi1, lo1;
+        if constexpr (WIDE) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+            hi0 = (uint32_t)(p0 >> 32);
+            lo0 = (uint32_t)p0;
+            hi1 = (uint32_t)(p1 >> 32);
+            lo1 = (uint32_t)p1;
+        } else {
+            hi0 = __umulhi(0xD2511F53u, c.x);
+            lo0 = 0xD2511F53u * c.x;
+            hi1 = __umulhi(0xCD9E8D57u, c.z);
+            lo1 = 0xCD9E8D57u * c.z;
+        }
+        c = make_uint4(hi1 ^ c.y ^ K.k0[r], lo1, hi0 ^ c.w ^ K.k1[r], lo0);
+    }
+    return c;
+}
+
 // All WANT <= kDirChunk directions of a cell update in one pass, in the
 // stream order of draw_directions: the two attempts of block 0 (field pairs
 // 1 and 2), blocks 1 and 2 without a loop (every lane needs block 1 and
@@ -62,7 +99,7 @@ __device__ __forceinline__ void draw_directions(const Geometry& g, uint32_t swee
 // than WANT (at most max(8, WANT + 2) <= kDirRows), in rows of sdir that no
 // trial reads; the stream is not continued.
 template <int ROWS, int WANT>
-__device__ __forceinline__ void draw_directions_once(const Geometry& g, uint32_t sweep, uint32_t cell, uint32_t c2,
+__device__ __forceinline__ void draw_directions_once(const PhiloxKeys& K, uint32_t sweep, uint32_t cell, uint32_t c2,
                                                      const uint32_t F0[6], float2 (*__restrict__ sdir)[32 * ROWS],
                                                      int tid) {
     static_assert(WANT <= kDirChunk && kDirRows >= kDirChunk + 2 && kDirRows >= 8, "sdir rows");
@@ -79,14 +116,14 @@ __device__ __forceinline__ void draw_directions_once(const Geometry& g, uint32_t
 #pragma unroll
     for (uint32_t blk = 1; blk < 3; ++blk) {   // every lane needs block 1, nearly every warp block 2
         uint32_t F[6];
-        fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+        fields21(philox_rk<(WANT > 4)>(make_uint4(sweep, cell, c2, blk), K), F);
         attempt(F[0], F[1]);
         attempt(F[2], F[3]);
         attempt(F[4], F[5]);
     }
     for (uint32_t blk = 3; have < WANT; ++blk) {
         uint32_t F[6];
-        fields21(philox4x32_10(make_uint4(sweep, cell, c2, blk), g.key0, g.key1), F);
+        fields21(philox_rk<(WANT > 4)>(make_uint4(sweep, cell, c2, blk), K), F);
         attempt(F[0], F[1]);
         attempt(F[2], F[3]);
         attempt(F[4], F[5]);
@@ -140,14 +177,19 @@ __device__ __forceinline__ void subsweep_f32(const Geometry& g, float* __restric
     const uint32_t cell = (uint32_t)(cy + g.row0) * (uint32_t)g.mx + (uint32_t)cx;   // global cell number
     const uint32_t c2 = (kDomTrial << 28) | ((uint32_t)Q << 24);
     uint32_t F[6];
-    fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
-    const uint32_t f0 = F[0];   // shuffle draw
+    uint32_t f0;                 // shuffle draw: field 0 of block 0
     uint32_t blk = 0;
     int pnext = 1;               // next attempt: field pair 1 of block 0 (fields 2,3)
-    if constexpr (NSEL > 0 && NSEL <= kDirChunk)
-        draw_directions_once<ROWS, NSEL>(g, sweep, cell, c2, F, sdir, tid);
-    else
-        draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);
+    if constexpr (NSEL > 0 && NSEL <= kDirChunk) {
+        const PhiloxKeys K(g.key0, g.key1);
+        fields21(philox_rk<(NSEL > 4)>(make_uint4(sweep, cell, c2, 0u), K), F);
+        f0 = F[0];
+        draw_directions_once<ROWS, NSEL>(K, sweep, cell, c2, F, sdir, tid);
+    } else {
+        fields21(philox4x32_10(make_uint4(sweep, cell, c2, 0u), g.key0, g.key1), F);
+        f0 = F[0];
+        draw_directions<ROWS>(g, sweep, cell, c2, F, blk, pnext, min(kDirChunk, nsel), sdir, tid);   // refills F
+    }
 
     // 3. cell contents
     const int n = (own.x[0] >= 0.f) + (own.x[1] >= 0.f) + (own.x[2] >= 0.f) + (own.x[3] >= 0.f);
